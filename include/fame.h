@@ -1,0 +1,244 @@
+/*
+ * fame.h -- C ABI of the GB300 library for the null-space-free reduced Maxwell
+ * eigenproblem of Huang, Li, Li, Lin, Lin and Tian, "Eigenvalue problems of
+ * discrete curl operators on various lattices for simulating three
+ * dimensional photonic crystals" (arXiv:1806.10284).
+ *
+ * The library applies A_r = Sigma_r Q_r^* B^{-1} Q_r Sigma_r (eq. NFSEP,
+ * Section 5.2) with hand-written sm_103a FFT kernels, finds its smallest
+ * eigenvalues with a block LOBPCG on the GPU (complex64 or complex128
+ * applies, FP64 Rayleigh-Ritz), and returns the eps-gradient of eigenvalues.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  * n = n1 n2 n3.  Grid arrays are in vec order: index i + n1 (j + n2 k),
+ *    x index fastest (Section 1.3, Section 3).
+ *  * A vector of A_r has 2n complex entries laid out [2][n]: the Pi_1
+ *    coordinate block, then the Pi_2 coordinate block; within a block the
+ *    frequency index (p, q, r) is ordered p + n1 (q + n2 r).  This is a fixed
+ *    permutation of the column order of T in eq. (T).  A block of m vectors is
+ *    [m][2][n], vector-major.
+ *  * Complex numbers are interleaved (re, im): complex64 = two float,
+ *    complex128 = two double (the layout of float2 / double2).
+ *  * "device" pointers are CUDA device memory of the current device; "host"
+ *    pointers are ordinary host memory.  The caller owns every buffer it
+ *    passes; the library owns everything inside a context.
+ *  * stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is enqueued on it.  Calls that return host values
+ *    synchronise that stream before returning.
+ *  * Every call returns a fame_status; nothing aborts.  After a non-OK
+ *    status, fame_last_error(ctx) describes it (a thread-local copy is kept
+ *    for failures of fame_create, readable with fame_last_error(NULL)).
+ *  * A context is not thread safe: one host thread at a time.
+ */
+#ifndef FAME_H
+#define FAME_H
+
+#if defined(__GNUC__)
+#define FAME_API __attribute__((visibility("default")))
+#else
+#define FAME_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fame_ctx fame_ctx;
+
+typedef enum {
+    FAME_OK = 0,
+    FAME_E_ARG = 1,      /* bad argument (null pointer, size out of range)              */
+    FAME_E_LATTICE = 2,  /* no ordering of a1..a3 meets the Section 2.2 conditions,     */
+                         /* or the vectors are linearly dependent                       */
+    FAME_E_RADIX = 3,    /* a grid size has a prime factor other than 2, 3, 5, or is   */
+                         /* outside [2, 1024]                                           */
+    FAME_E_CUDA = 4,     /* a CUDA runtime call failed (message holds its name/error)   */
+    FAME_E_NOMEM = 5,    /* device or host allocation failed                           */
+    FAME_E_STATE = 6,    /* call out of order (e.g. gradient before eigs, no eps set)   */
+    FAME_E_NOCONV = 7,   /* eigensolver hit max_iter before the residual tolerance      */
+    FAME_E_TIMEOUT = 8   /* a bounded device wait gave up (batched solver)              */
+} fame_status;
+
+/* dtype of vectors passed to fame_apply_Ar / fame_lift */
+enum { FAME_C64 = 0, FAME_C128 = 1 };
+
+/* flags of fame_eigs */
+enum {
+    FAME_FP64 = 1,          /* complex128 applies throughout                          */
+    FAME_MIXED = 2,         /* complex64 applies, then complex128 refinement          */
+    FAME_DETERMINISTIC = 4, /* fixed reduction order (always true in this build)      */
+    FAME_WARM_START = 8     /* start from the context's last eigenvectors if present  */
+};
+
+/* Geometry chosen by fame_create (Section 2.2), for sampling eps on the Yee points. */
+typedef struct {
+    int n[3];          /* n1, n2, n3 along the canonical a1, a2, a3                   */
+    int perm[3];       /* input vector index used as canonical a1, a2, a3             */
+    int m[3];          /* grid offsets m1, m2, m3 after rounding                      */
+    int rho[3];        /* rho1, rho2, rho3 (obtuse-case indicators)                    */
+    int s[3];          /* index shifts: a2 <-> (s1, n2, 0), a3 <-> (s2, s3, n3)        */
+    double delta[3];   /* mesh sizes delta_x, delta_y, delta_z                         */
+    double a[9];       /* corrected vectors of eq. (transvec), column-major: a1, a2, a3 */
+    double kappa[3];   /* Bloch fractions kappa_l = k . a_l (eq. quasi_periodic)        */
+} fame_plan_info;
+
+/* Counters of the last fame_eigs call. */
+typedef struct {
+    int iters_mixed;        /* LOBPCG iterations with complex64 applies               */
+    int iters_fp64;         /* LOBPCG iterations with complex128 applies               */
+    long long applies_c64;  /* single-vector A_r applies, complex64                    */
+    long long applies_c128; /* single-vector A_r applies, complex128                   */
+    double max_residual;    /* max_j ||A_r y_j - lambda_j y_j|| / lambda_j (FP64 apply) */
+} fame_solve_stats;
+
+/*
+ * fame_create -- plan one lattice and Bloch vector (Section 2.2, eq. transvec).
+ *   out      : receives the new context (host pointer to a pointer).
+ *   lattice  : Bravais lattice id 0..13, or 14 = generic; informational only.
+ *   a1,a2,a3 : primitive vectors (host, 3 doubles each), any Cartesian frame.
+ *   n1,n2,n3 : grid sizes along the canonical a1, a2, a3 (the vectors after
+ *              the ordering of Section 2.2: a1 the longest, the sin(gamma)
+ *              condition met); each in [2, 1024] with prime factors 2, 3, 5.
+ *   bloch    : the Bloch vector 2*pi*k (host, 3 doubles), same frame as a_l.
+ * The vectors are reordered, rotated to the upper-triangular form, the grid
+ * offsets m1, m2, m3 rounded (floor below 1/2, ceiling otherwise) and the
+ * angles corrected so that a2 and a3 end on grid points.  Uses the current
+ * CUDA device.  Errors: FAME_E_ARG, FAME_E_LATTICE, FAME_E_RADIX,
+ * FAME_E_CUDA, FAME_E_NOMEM; *out is NULL on failure.
+ */
+FAME_API fame_status fame_create(fame_ctx** out, int lattice, const double a1[3], const double a2[3],
+                        const double a3[3], int n1, int n2, int n3, const double bloch[3]);
+
+/*
+ * fame_plan_lattice -- host only, no GPU needed: the geometry fame_create
+ * would choose for these arguments (same meaning as fame_create), written to
+ * *info.  Errors: FAME_E_ARG, FAME_E_LATTICE, FAME_E_RADIX (message via
+ * fame_last_error(NULL)).
+ */
+FAME_API fame_status fame_plan_lattice(const double a1[3], const double a2[3], const double a3[3],
+                                       int n1, int n2, int n3, const double bloch[3],
+                                       fame_plan_info* info);
+
+/* fame_get_plan -- copy the chosen geometry (host struct). */
+FAME_API fame_status fame_get_plan(const fame_ctx* ctx, fame_plan_info* info);
+
+/*
+ * fame_set_k -- change the Bloch vector 2*pi*k (host, 3 doubles) of a context:
+ * rebuilds only the twist-phase tables (Section 4.2, eq. diagonal_matrix).
+ * Invalidates stored eigenvectors' warm start only if the grid changes (it
+ * does not).  Errors: FAME_E_ARG, FAME_E_CUDA.
+ */
+FAME_API fame_status fame_set_k(fame_ctx* ctx, const double bloch[3]);
+
+/*
+ * fame_set_eps -- set B = diag(vec B1, vec B2, vec B3) (Section 3): the
+ * permittivity sampled at the E1, E2, E3 Yee points (i+1/2, j, k),
+ * (i, j+1/2, k), (i, j, k+1/2) of the canonical grid.
+ *   B1,B2,B3 : host arrays of n doubles each, vec order, every value > 0.
+ * The library keeps 1/B in float and double on the device.  Errors:
+ * FAME_E_ARG (null, non-positive or non-finite value), FAME_E_CUDA.
+ */
+FAME_API fame_status fame_set_eps(fame_ctx* ctx, const double* B1, const double* B2, const double* B3,
+                         void* stream);
+
+/* fame_set_eps_device -- as fame_set_eps with B a device array [3][n] of doubles. */
+FAME_API fame_status fame_set_eps_device(fame_ctx* ctx, const double* B, void* stream);
+
+/*
+ * fame_apply_Ar -- Ay = A_r y = Sigma_r Q_r^* B^{-1} Q_r Sigma_r y (eq. NFSEP),
+ * Q_r = (I_3 (x) T)[Pi_1 Pi_2] with T applied by twisted FFTs (Algorithms
+ * 5.1 and 5.2) and Pi_1, Pi_2, Sigma_r of eqs. (range_basis1), (range_basis2),
+ * (SVD).
+ *   y, Ay : device, [m][2][n] complex of type dtype; may not overlap.
+ *   m     : number of vectors, 1 <= m <= 4096.
+ *   dtype : FAME_C64 or FAME_C128.
+ * Asynchronous on stream.  Errors: FAME_E_ARG, FAME_E_STATE (no eps set),
+ * FAME_E_NOMEM (workspace), FAME_E_CUDA.
+ */
+FAME_API fame_status fame_apply_Ar(fame_ctx* ctx, const void* y, void* Ay, int m, int dtype, void* stream);
+
+/*
+ * fame_lift -- x = B^{-1} Q_r Sigma_r y, the GEP eigenvector for an A_r
+ * eigenvector y (below Theorem invariant_space).
+ *   y : device [m][2][n]; x : device [m][3][n] (E1, E2, E3 on the Yee grid);
+ *   complex of type dtype.  Asynchronous.  Errors as fame_apply_Ar.
+ */
+FAME_API fame_status fame_lift(fame_ctx* ctx, const void* y, void* x, int m, int dtype, void* stream);
+
+/*
+ * fame_eigs -- the nev smallest (nonzero) eigenvalues of A_r, which are the
+ * nev smallest nonzero eigenvalues of C^*C e = lambda B e (eq. GEP; Theorem
+ * invariant_space).  Block LOBPCG with the preconditioner
+ * Sigma_r^{-2} / mean(B^{-1}); Gram matrices accumulated in FP64 and the
+ * Rayleigh-Ritz problem solved in FP64.  With FAME_MIXED the iteration runs
+ * on complex64 applies and is then refined with complex128 applies; with
+ * FAME_FP64 it runs on complex128 throughout.  Converged when
+ * ||A_r y_j - lambda_j y_j|| <= tol * lambda_j (||y_j|| = 1, complex128
+ * apply) for every j < nev.  At 2*pi*k = 0 the two zero eigenvalues of the
+ * zero-frequency coordinates are excluded.
+ *   nev        : 1 <= nev <= 64.
+ *   tol        : residual tolerance (e.g. 1e-8), > 0.
+ *   max_iter   : iteration cap for the whole solve (both phases).
+ *   flags      : FAME_MIXED or FAME_FP64, optionally | FAME_WARM_START.
+ *   lambda_out : host, nev doubles, ascending.
+ *   Y_out      : device [nev][2][n] complex128 unit eigenvectors, or NULL.
+ *   iters_out  : host int (total iterations), or NULL.
+ * The eigenpairs are also kept in the context for fame_grad_eps.
+ * Synchronises stream.  Errors: FAME_E_ARG, FAME_E_STATE, FAME_E_NOCONV
+ * (lambda_out still holds the best values), FAME_E_NOMEM, FAME_E_CUDA.
+ */
+FAME_API fame_status fame_eigs(fame_ctx* ctx, int nev, double tol, int max_iter, int flags,
+                      double* lambda_out, void* Y_out, int* iters_out, void* stream);
+
+/* fame_get_stats -- counters of the last fame_eigs (host struct). */
+FAME_API fame_status fame_get_stats(const fame_ctx* ctx, fame_solve_stats* stats);
+
+/*
+ * fame_grad_eps -- dB = sum_j dobj_dlambda[j] * d lambda_j / d B, with
+ * d lambda_j / d B_l(v) = -|x_{j,l}(v)|^2, x_j = B^{-1} Q_r Sigma_r y_j
+ * (Hellmann-Feynman on eq. NFSEP; A_r depends on B only through B^{-1}),
+ * using the eigenpairs of the last fame_eigs call.  Bands whose eigenvalues
+ * differ by at most rel_cluster * lambda form a cluster; every member gets
+ * the cluster mean of -|x_j|^2.
+ *   nev          : number of leading bands used, <= the last solve's nev.
+ *   dobj_dlambda : host, nev doubles.
+ *   rel_cluster  : degeneracy threshold (e.g. 1e-8 after FP64 refinement).
+ *   dB_out       : device [3][n] doubles (overwritten).
+ * Synchronises stream.  Errors: FAME_E_ARG, FAME_E_STATE (no solve yet),
+ * FAME_E_CUDA.
+ */
+FAME_API fame_status fame_grad_eps(fame_ctx* ctx, int nev, const double* dobj_dlambda, double rel_cluster,
+                          double* dB_out, void* stream);
+
+/*
+ * fame_eigs_batched -- solve several contexts (lattices and Bloch vectors,
+ * grids may differ) in lock-step: each LOBPCG iteration of every problem is
+ * one captured CUDA graph replay; problems that converge drop out.
+ *   ctxs       : host array of nprob context pointers (eps set on each).
+ *   nev, tol, max_iter, flags : as fame_eigs (FAME_MIXED or FAME_FP64).
+ *   lambda_out : host [nprob][nev] doubles.
+ *   iters_out  : host [nprob] ints, or NULL.
+ * Synchronises stream.  Errors: as fame_eigs; FAME_E_NOCONV if any problem
+ * did not converge.
+ */
+FAME_API fame_status fame_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol,
+                              int max_iter, int flags, double* lambda_out, int* iters_out,
+                              void* stream);
+
+/* fame_last_error -- message of the last failure on ctx (or of fame_create if ctx is NULL). */
+FAME_API const char* fame_last_error(const fame_ctx* ctx);
+
+/* fame_destroy -- free a context and its device memory; NULL is ignored. */
+FAME_API void fame_destroy(fame_ctx* ctx);
+
+/* fame_launch_count -- kernels this library has launched in this process (monotone). */
+FAME_API unsigned long long fame_launch_count(void);
+
+/* fame_version -- library version string. */
+FAME_API const char* fame_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FAME_H */

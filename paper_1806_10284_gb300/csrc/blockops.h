@@ -1,0 +1,48 @@
+// Block operations used by the eigensolver (definitions in blockops.cu).
+#pragma once
+#include "fame_internal.h"
+
+// Up to three column blocks of vectors (each column = 2n complex, leading dim ld).
+template <typename C>
+struct BlockList {
+    const C* ptr[3];
+    int cols[3];
+    int total;
+};
+
+template <typename C>
+inline BlockList<C> blocks(const C* a, int na, const C* b = nullptr, int nb = 0,
+                           const C* c = nullptr, int nc = 0) {
+    BlockList<C> L;
+    L.ptr[0] = a; L.cols[0] = na;
+    L.ptr[1] = b; L.cols[1] = nb;
+    L.ptr[2] = c; L.cols[2] = nc;
+    L.total = na + nb + nc;
+    return L;
+}
+
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { using T = float; };
+template <> struct RealOf<double2> { using T = double; };
+
+// G (column-major ku x kv, double2, device) = U^H V
+template <typename C>
+fame_status gram(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V, size_t ld, double2* G,
+                 cudaStream_t st);
+// out1 = S M[:, :m], out2 = S[:, i0:] M[i0:, :m]  (either output may be null)
+template <typename C, typename Co>
+fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2* M, int m, int i0,
+                    Co* out1, Co* out2, cudaStream_t st);
+// W = tinv .* (AX - X theta) (W may be null), part[j][blk] = partial ||R_j||^2
+template <typename C>
+fame_status residual(fame_ctx* c, const C* X, const C* AX, const double* theta_dev,
+                     const typename RealOf<C>::T* tinv, int m, C* W, double* part, int nblk,
+                     cudaStream_t st);
+template <typename Ci, typename Co>
+fame_status convert(fame_ctx* c, const Ci* in, Co* out, size_t N, cudaStream_t st);
+template <typename C>
+fame_status random_block(fame_ctx* c, C* X, int m, uint64_t seed,
+                         const typename RealOf<C>::T* tinv, cudaStream_t st);
+template <typename C>
+fame_status mask_block(fame_ctx* c, C* X, int m, const typename RealOf<C>::T* tinv,
+                       cudaStream_t st);

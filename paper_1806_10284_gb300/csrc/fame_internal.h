@@ -1,0 +1,182 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fame.h"
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename R> struct cpx;
+template <> struct cpx<float> { using T = float2; };
+template <> struct cpx<double> { using T = double2; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+template <typename C>
+__host__ __device__ __forceinline__ C cmul(C a, C b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// conj(a) * b
+template <typename C>
+__host__ __device__ __forceinline__ C cmulc(C a, C b) { return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+template <typename C>
+__host__ __device__ __forceinline__ C conjc(C a) { return mk(a.x, -a.y); }
+
+// ---------------------------------------------------------------------------
+// Lattice plan (Section 2.2)
+// ---------------------------------------------------------------------------
+struct LatticePlan {
+    int n[3];
+    int perm[3];
+    int m[3];
+    int rho[3];
+    int s[3];
+    double delta[3];
+    double a[3][3];      // a[row][col]: column l is a_l of eq. (transvec)
+    double kappa[3];
+    double len[3];
+    double cos_in[3];    // gamma', beta', alpha'
+    double cos_c[3];     // corrected gamma, beta, alpha
+};
+
+// Returns an empty string on success, else the reason.
+std::string build_lattice(const double* a1, const double* a2, const double* a3, int n1, int n2,
+                          int n3, const double* bloch, LatticePlan* out);
+void compute_kappa(const double* a1, const double* a2, const double* a3, const double* bloch,
+                   LatticePlan* plan);
+// radix list of a length (factors 8, 4, 2, 3, 5); empty if unsupported
+std::vector<int> radix_list(int L);
+
+// ---------------------------------------------------------------------------
+// Per-axis FFT plan, passed to kernels by value.
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 12;
+struct AxisPlan {
+    int L;
+    int nst;
+    int radix[kMaxStages];
+};
+
+// Twist-fraction representation.  For complex64 kernels a fraction f in
+// [0, 1) is split into hi (a multiple of 2^-13) and lo = f - hi so that
+// products idx * hi with idx < 1024 are exact in float.
+struct Frac32 { float hi, lo; };
+
+template <typename R> struct FracT;
+template <> struct FracT<float> { using T = Frac32; };
+template <> struct FracT<double> { using T = double; };
+
+// Everything a transform kernel needs about one (lattice, k).
+template <typename R>
+struct KParams {
+    int n1, n2, n3;
+    R inv_dx, inv_dy, inv_dz;
+    typename FracT<R>::T f1;           // c1 / n1 mod 1
+    const typename FracT<R>::T* f2;    // [n1]   c2(p) / n2 mod 1
+    const typename FracT<R>::T* f3;    // [n2][n1] c3(p, q) / n3 mod 1
+    const typename cpx<R>::T* tw[3];   // per-axis e^{-2 pi i t / L}
+    AxisPlan ax[3];
+    const R* invB;                     // [3][n] 1/B
+    const uint32_t* alt;               // [ceil(n/32)] reference-vector decision bits
+    R scale;                           // 1/n for a full apply
+};
+
+// Device tables of one precision.
+template <typename R>
+struct DevTables {
+    typename FracT<R>::T* f2 = nullptr;
+    typename FracT<R>::T* f3 = nullptr;
+    typename cpx<R>::T* tw[3] = {nullptr, nullptr, nullptr};
+    R* invB = nullptr;
+    R* tinv = nullptr;   // [n] preconditioner 1/(Lambda_q mean(1/B)), 0 where Lambda_q = 0
+    typename FracT<R>::T f1;
+};
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct GrowBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct fame_ctx {
+    LatticePlan plan;
+    double in_vec[3][3];           // the primitive vectors as given (for kappa)
+    int device = 0;
+    long long n = 0;
+    DevTables<float> tf;
+    DevTables<double> td;
+    uint32_t* alt_mask = nullptr;  // reference-vector decision per frequency (FP64)
+    bool eps_set = false;
+    double mean_invB = 0.0;
+    GrowBuf work;                  // transform workspace [m][3][n] complex
+    // solver state
+    std::vector<double> lambda;    // last eigenvalues
+    double* Y = nullptr;           // device [nev][2][n] complex128 eigenvectors
+    int Y_nev = 0;
+    GrowBuf solver;                // solver blocks
+    GrowBuf partial;               // Gram partial sums
+    fame_solve_stats stats{};
+    std::string err;
+};
+
+// error helpers
+fame_status set_err(fame_ctx* c, fame_status s, const std::string& msg);
+#define FAME_CUDA_TRY(ctx, call)                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return set_err((ctx), FAME_E_CUDA,                                               \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+fame_status grow(fame_ctx* c, GrowBuf& b, size_t bytes);
+void count_launch(int k = 1);
+
+// tables (plan.cpp / tables.cu)
+fame_status build_tables(fame_ctx* c);      // twiddles, twist fractions, preconditioner
+fame_status build_precond(fame_ctx* c, cudaStream_t st);
+template <typename R> KParams<R> make_params(const fame_ctx* c);
+template <> KParams<float> make_params<float>(const fame_ctx* c);
+template <> KParams<double> make_params<double>(const fame_ctx* c);
+// 1/B in float and double from a device [3][n] array; returns mean(1/B)
+fame_status eps_from_device(fame_ctx* c, const double* B, cudaStream_t st, double* mean_invB);
+
+// transforms (transforms.cu)
+template <typename R>
+fame_status run_apply(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* Ay, int m,
+                      cudaStream_t st);
+template <typename R>
+fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* x, int m,
+                     cudaStream_t st);
+fame_status run_grad(fame_ctx* c, const double2* Y, const double* w, int nev, double* dB,
+                     cudaStream_t st);
+fame_status run_precond_table(fame_ctx* c, cudaStream_t st);
+fame_status run_basis_mask(fame_ctx* c);
+
+// solver (solver.cu)
+fame_status run_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol, int max_iter,
+                             int flags, double* lambda_out, int* iters_out, cudaStream_t st);
+fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, double* lambda_out,
+                     void* Y_out, int* iters_out, cudaStream_t st);
+
+// small dense FP64 Rayleigh-Ritz (rr.cpp): solve GA c = theta GB c for the k x k
+// Hermitian pair (column-major complex, interleaved), return the nwant smallest
+// pairs.  drop: relative threshold on the scaled GB spectrum below which
+// directions are discarded.  Returns the number of pairs produced.
+int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double drop,
+                  double* theta, double* C);
+// Hermitian eigensolver (ascending), A column-major k x k complex; V may alias nothing.
+void herm_eig(int k, const double* A, double* w, double* V);

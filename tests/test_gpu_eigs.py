@@ -1,0 +1,180 @@
+"""GPU eigensolver and eps-gradient against the CPU oracle (through the C ABI).
+
+Eigenvalue tolerances (relative): 1e-10 for the FP64 path, 1e-5 for the mixed
+path; residual ||A_r y - lambda y|| <= tol * lambda after refinement, measured
+with the library's complex128 apply (itself parity-tested in test_gpu_apply).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.eigs import eigs_dense, lobpcg
+from oracle.grad import objective_gradient
+from oracle.lattice import make_lattice
+from paper_1806_10284_gb300 import fame
+from paper_1806_10284_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1806_10284_gb300 import build
+    build.build()
+    fame.load()
+
+
+def _small(name, n, seed, kred=None):
+    w = W.WORKLOADS[name]
+    rng = np.random.default_rng(seed)
+    kr = rng.uniform(-0.5, 0.5, 3) if kred is None else np.asarray(kred, float)
+    K = W.bloch_from_reduced(w["vectors"], kr)
+    lat = make_lattice(w["vectors"], n, K)
+    B = np.stack([1.0 + 12.0 * (rng.random(lat.shape) < 0.3) for _ in range(3)])
+    ctx = fame.Context(w["vectors"], n, K)
+    ctx.set_eps(*B)
+    return lat, ctx, B
+
+
+def _residuals(ctx, lam, Y):
+    AY = ctx.apply(Y)
+    R = AY - torch.as_tensor(lam, device="cuda")[:, None] * Y
+    return (torch.linalg.vector_norm(R, dim=1) / torch.as_tensor(lam, device="cuda")).cpu().numpy()
+
+
+@pytest.mark.parametrize("name,n", [("fcc64", (6, 6, 6)), ("tri192", (8, 6, 5)),
+                                    ("hex96", (8, 8, 5)), ("bcc96", (6, 6, 6))])
+@pytest.mark.parametrize("flags,rtol", [(fame.FAME_FP64, 1e-10), (fame.FAME_MIXED, 1e-9)])
+def test_eigs_small_vs_dense(name, n, flags, rtol):
+    lat, ctx, B = _small(name, n, seed=7)
+    ref, _ = eigs_dense(lat, 1.0 / B, 8)
+    lam, Y, it = ctx.eigs(8, tol=1e-11, flags=flags, vectors=True)
+    np.testing.assert_allclose(lam, ref, rtol=rtol)
+    assert np.all(_residuals(ctx, lam, Y) <= 1e-11 * 1.01)
+    st = ctx.stats()
+    assert st["max_residual"] <= 1e-11
+    if flags == fame.FAME_MIXED:
+        assert st["applies_c64"] > 0
+
+
+def test_eigs_gamma_excludes_zero_modes():
+    lat, ctx, B = _small("fcc64", (6, 6, 6), seed=3, kred=[0.0, 0.0, 0.0])
+    ref, _ = eigs_dense(lat, 1.0 / B, 6)
+    lam, _, _ = ctx.eigs(6, tol=1e-11, flags=fame.FAME_FP64)
+    assert lam[0] > 1e-3
+    np.testing.assert_allclose(lam, ref, rtol=1e-10)
+
+
+def test_config_sc16_fp64():
+    """Simple cubic 16^3, sphere eps 13, K = pi (0.5, 0.1, 0.2), 10 bands, complex128 throughout,
+    residual 1e-10; oracle: FP64 LOBPCG to 1e-11."""
+    name = "sc16"
+    w = W.WORKLOADS[name]
+    K = W.bloch_vectors(name)[0]
+    lat = make_lattice(w["vectors"], w["n"], K)
+    geom = fame.geometry_of(fame.plan_lattice(w["vectors"], w["n"], K))
+    B = np.stack(W.eps_for(name, geom))
+    ref, _, _, _ = lobpcg(lat, 1.0 / B, 10, block=16, tol=1e-11, seed=5)
+    ctx = fame.Context(w["vectors"], w["n"], K, lattice=0)
+    ctx.set_eps(*B)
+    lam, Y, it = ctx.eigs(10, tol=1e-10, flags=fame.FAME_FP64, vectors=True)
+    np.testing.assert_allclose(lam, ref, rtol=1e-10)
+    assert np.all(_residuals(ctx, lam, Y) <= 1e-10 * 1.01)
+
+
+def test_config_sc16_mixed():
+    name = "sc16"
+    w = W.WORKLOADS[name]
+    K = W.bloch_vectors(name)[0]
+    lat = make_lattice(w["vectors"], w["n"], K)
+    geom = fame.geometry_of(fame.plan_lattice(w["vectors"], w["n"], K))
+    B = np.stack(W.eps_for(name, geom))
+    ref, _, _, _ = lobpcg(lat, 1.0 / B, 10, block=16, tol=1e-11, seed=5)
+    ctx = fame.Context(w["vectors"], w["n"], K, lattice=0)
+    ctx.set_eps(*B)
+    lam, Y, it = ctx.eigs(10, tol=1e-8, flags=fame.FAME_MIXED, vectors=True)
+    np.testing.assert_allclose(lam, ref, rtol=1e-5)
+    assert np.all(_residuals(ctx, lam, Y) <= 1e-8 * 1.01)
+
+
+def test_warm_start_reuses_vectors():
+    lat, ctx, B = _small("mono80", (10, 12, 8), seed=2)
+    lam0, _, it0 = ctx.eigs(6, tol=1e-10, flags=fame.FAME_FP64)
+    lam1, _, it1 = ctx.eigs(6, tol=1e-10, flags=fame.FAME_FP64 | fame.FAME_WARM_START)
+    np.testing.assert_allclose(lam1, lam0, rtol=1e-9)
+    assert it1 < it0
+
+
+@pytest.mark.parametrize("flags", [fame.FAME_FP64, fame.FAME_MIXED])
+def test_gradient_vs_oracle(flags):
+    """d obj / d B for obj = sum_j c_j lambda_j against the oracle's Hellmann-Feynman
+    gradient from its own dense eigenpairs (cluster-averaged, so vector phases and
+    degenerate subspaces do not matter)."""
+    lat, ctx, B = _small("tri192", (8, 6, 5), seed=11)
+    nev = 6
+    lam_ref, V = eigs_dense(lat, 1.0 / B, nev)
+    c = np.linspace(1.0, -0.5, nev)
+    g_ref = objective_gradient(lat, 1.0 / B, V, lam_ref, c, rel_tol=1e-8)
+    lam, _, _ = ctx.eigs(nev, tol=1e-11, flags=flags)
+    g = ctx.grad(nev, c, rel_cluster=1e-8).cpu().numpy().reshape(g_ref.shape)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-7, atol=1e-9 * np.abs(g_ref).max())
+
+
+def test_gradient_central_differences_gpu():
+    """Central differences (step 1e-4) of GPU FP64 eigensolves on random voxels."""
+    lat, ctx, B = _small("sc16", (8, 8, 6), seed=4)
+    nev = 5
+    lam, _, _ = ctx.eigs(nev, tol=1e-12, flags=fame.FAME_FP64)
+    gaps = np.diff(lam) / lam[:-1]
+    j = int(np.argmax(np.minimum(np.r_[1.0, gaps], np.r_[gaps, 1.0])))
+    e = np.zeros(nev)
+    e[j] = 1.0
+    g = ctx.grad(nev, e, rel_cluster=1e-8).cpu().numpy().reshape(B.shape)
+    rng = np.random.default_rng(1)
+    h = 1e-4
+    for _ in range(8):
+        idx = tuple(int(rng.integers(0, s)) for s in B.shape)
+        vals = []
+        for sgn in (1, -1):
+            Bp = B.copy()
+            Bp[idx] += sgn * h
+            ctx.set_eps(*Bp)
+            vals.append(ctx.eigs(nev, tol=1e-12, flags=fame.FAME_FP64)[0][j])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert g[idx] == pytest.approx(fd, rel=1e-4, abs=1e-7 * lam[j])
+    ctx.set_eps(*B)
+
+
+def test_gradient_euler_sum_rule_full_size():
+    """sum_{l,v} B_l(v) d lambda_j / d B_l(v) = -lambda_j at the 48^3 smooth-field workload."""
+    name = "sc48grad"
+    w = W.WORKLOADS[name]
+    K = W.bloch_vectors(name)[0]
+    geom = fame.geometry_of(fame.plan_lattice(w["vectors"], w["n"], K))
+    B = np.stack(W.eps_for(name, geom))
+    ctx = fame.Context(w["vectors"], w["n"], K, lattice=0)
+    ctx.set_eps(*B)
+    nev = 6
+    lam, _, _ = ctx.eigs(nev, tol=1e-9, flags=fame.FAME_MIXED)
+    for j in (4, 5):
+        e = np.zeros(nev)
+        e[j] = 1.0
+        g = ctx.grad(nev, e, rel_cluster=0.0).cpu().numpy().reshape(B.shape)
+        assert float(np.sum(B * g)) == pytest.approx(-lam[j], rel=1e-8)
+
+
+def test_autograd_function():
+    lat, ctx, B = _small("fcc64", (6, 6, 6), seed=9)
+    EigGrad = fame.eig_grad_function()
+    Bt = torch.as_tensor(B.reshape(-1), device="cuda").requires_grad_(True)
+    lam = EigGrad.apply(Bt, ctx, 6, 1e-11, fame.FAME_FP64, 1e-8)
+    obj = (lam[5] - lam[4]) / lam[4]
+    obj.backward()
+    lam_ref, V = eigs_dense(lat, 1.0 / B, 6)
+    c = np.zeros(6)
+    c[5] = 1.0 / lam_ref[4]
+    c[4] = -lam_ref[5] / lam_ref[4] ** 2
+    g_ref = objective_gradient(lat, 1.0 / B, V, lam_ref, c, rel_tol=1e-8).ravel()
+    np.testing.assert_allclose(Bt.grad.cpu().numpy(), g_ref, rtol=1e-7,
+                               atol=1e-9 * np.abs(g_ref).max())
