@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the reduced-operator eigensolver on one or more GB300 GPUs.
+
+One step = one pass of the whole hot path over one synthetic problem: the 10
+smallest eigenvalues of A_r for the FCC 64^3 diamond-sphere workload (complex64
+applies, FP64 Rayleigh-Ritz and complex128 refinement to residual 1e-8) and
+the eps-gradient of their sum.  ``value`` is A_r applies per second over the
+timed steps (every single-vector apply either precision performed, summed over
+ranks, divided by the slowest rank's time); ``time_to_10_bands_s`` is the
+eigensolve part of a step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own Bloch vector (independent problems,
+no data-path collective: weak scaling).  ``--impl reference`` times the CPU
+oracle (FP64 numpy) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "fcc64"
+NEV = 10
+TOL = 1e-8
+METRIC = "A_r applies/sec and time-to-10-bands at 1e-8 residual; fused-FFT HBM GB/s vs peak"
+UNIT = "A_r applies/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_inputs(rank):
+    """Vectors, grid, Bloch vector of this rank (rank 0: the workload's own k)."""
+    from paper_1806_10284_gb300 import workloads as W
+    w = W.WORKLOADS[WORKLOAD]
+    red = np.array(w["reduced_k"][0], dtype=np.float64)
+    if rank > 0:
+        red = red + np.array([0.013, -0.007, 0.011]) * rank
+    return w["vectors"], w["n"], W.bloch_from_reduced(w["vectors"], red)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (the reference arm and the cpu_baseline field)
+# ---------------------------------------------------------------------------
+def oracle_apply_rate(seconds, rank=0, min_vectors=2):
+    """Oracle FP64 A_r applies/s on random vectors of the workload (single process)."""
+    from oracle.lattice import make_lattice
+    from oracle.nfsep import apply_Ar, bases
+    from paper_1806_10284_gb300 import workloads as W
+    vec, n, K = workload_inputs(rank)
+    lat = make_lattice(vec, n, K)
+    geom = W.Geometry(n=n, s=(lat.s1, lat.s2, lat.s3), delta=(lat.dx, lat.dy, lat.dz), perm=lat.perm)
+    B = W.eps_for(WORKLOAD, geom)
+    invB = np.stack([1.0 / b for b in B])
+    b = bases(lat)
+    rng = np.random.default_rng(0)
+    done, t0 = 0, time.perf_counter()
+    while done < min_vectors or time.perf_counter() - t0 < seconds:
+        y = rng.standard_normal((2,) + lat.shape) + 1j * rng.standard_normal((2,) + lat.shape)
+        apply_Ar(lat, y, invB, b)
+        done += 1
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 peak of a GB300 (nominal FP64 rate of the profiling recipe's table)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("transforms.cu", "blockops.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1806_10284_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+def roofline(prof):
+    hbm, kind = measured_peaks()
+    if not prof:
+        return None
+    name, st = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    secs = st["total_ms"] / 1e3
+    if name.endswith("c128"):
+        ach = st["flops"] / secs / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic_for(name),
+                "peak_source": "nominal FP64 rate (recipe table)",
+                "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"],
+                "share_of_kernel_time": st["total_ms"] / sum(v["total_ms"] for v in prof.values())}
+    ach = st["bytes"] / secs / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": traffic_for(name),
+            "peak_source": f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else "fallback 6.8 TB/s",
+            "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"],
+            "bytes_per_launch": st["bytes"] / st["launches"],
+            "share_of_kernel_time": st["total_ms"] / sum(v["total_ms"] for v in prof.values())}
+
+
+# ---------------------------------------------------------------------------
+# the two arms
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sample = 4
+    for _ in range(args.warmup):
+        oracle_apply_rate(0.0, min_vectors=1)
+    t = 0.0
+    done = 0
+    for _ in range(args.steps):
+        rate, d, dt = oracle_apply_rate(0.0, min_vectors=sample)
+        t += dt
+        done += d
+    value = done / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "fcc64: FCC primitive (a/2)(0,1,1),(a/2)(1,0,1),(a/2)(1,1,0), 64^3, "
+                                  "eps=13 diamond-site spheres, A_r applies (oracle: FP64 numpy)",
+                      "sample_per_step": f"{sample} single-vector A_r applies"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} steps x {sample} FP64 applies at FCC 64^3, "
+                                      "single process (numpy FFT)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before any GPU work: oracle FP64 applies on host cores, bounded sample
+        rate, done, dt = oracle_apply_rate(args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} FP64 single-vector A_r applies at FCC 64^3 in {dt:.1f} s "
+                         "(numpy FFT, one process)"}
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1806_10284_gb300 import fame
+    from paper_1806_10284_gb300 import workloads as W
+    fame.load()
+    vec, n, K = workload_inputs(rank)
+    ctx = fame.Context(vec, n, K, lattice=2)
+    B = W.eps_for(WORKLOAD, ctx.geometry())
+    ctx.set_eps(*B)
+    Bdev = torch.as_tensor(np.stack(B).reshape(-1), device="cuda")
+    ctx.set_eps_device(Bdev)
+    dobj = np.ones(NEV)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        lam, _, it = ctx.eigs(NEV, tol=TOL, max_iter=600, flags=fame.FAME_MIXED)
+        st = ctx.stats()
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record()
+        ctx.grad(NEV, dobj, rel_cluster=1e-8)
+        return lam, st, ev
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    fame.profile(True)
+    launches0 = fame.launch_count()
+    total_ms = 0.0
+    eig_ms = 0.0
+    applies = 0
+    applies64 = 0
+    resid = 0.0
+    for _ in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (512 MiB write)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lam, st, emid = step()
+        e1.record()
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        eig_ms += e0.elapsed_time(emid)
+        applies += st["applies_c64"] + st["applies_c128"]
+        applies64 += st["applies_c128"]
+        resid = max(resid, st["max_residual"])
+    launches = fame.launch_count() - launches0
+    fame.profile(False)
+    prof = fame.profile_read()
+    clk = clocks.stop()
+    # max over ranks of the timed region, sum of work
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, eig_ms], dtype=torch.float64, device="cuda")
+        a = torch.tensor([float(applies), float(launches)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        total_ms, eig_ms = float(t[0]), float(t[1])
+        applies, launches = int(a[0]), int(a[1])
+    value = applies / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned), H2D and D2H inside
+    Bh = torch.as_tensor(np.stack(B).reshape(3, -1)).pin_memory()
+    dB_h = torch.empty((3, ctx.N), dtype=torch.float64).pin_memory()
+    Bnp = Bh.numpy()
+    e2e_applies = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_eps(Bnp[0], Bnp[1], Bnp[2])             # H2D of the step's input
+        lam, _, _ = ctx.eigs(NEV, tol=TOL, max_iter=600, flags=fame.FAME_MIXED)   # lambda D2H
+        st = ctx.stats()
+        e2e_applies += st["applies_c64"] + st["applies_c128"]
+        dB = ctx.grad(NEV, dobj, rel_cluster=1e-8)
+        dB_h.copy_(dB)                                  # D2H of the gradient
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        a = torch.tensor([float(e2e_applies)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        e2e_s, e2e_applies = float(t[0]), int(a[0])
+    if rank != 0:
+        return
+    rl = roofline(prof)
+    m = NEV + max(4, (NEV + 1) // 2)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "fp32 complex64 FFT apply + fp64 refinement/Rayleigh-Ritz",
+           "data": "synthetic (seeded eps=13 diamond-site spheres on the Yee grid)",
+           "config": {"workload": "fcc64: FCC primitive (a/2)(0,1,1),(a/2)(1,0,1),(a/2)(1,1,0), "
+                                  "grid 64^3, eps=13 spheres r=0.325*sqrt(3)/4 at (0,0,0),(1/4,1/4,1/4), "
+                                  "10 bands at one k per rank, residual 1e-8, + eps-gradient",
+                      "nev": NEV, "tol": TOL, "block": m, "grid": list(n),
+                      "l2": "512 MiB buffer written between timed steps (L2 flush); "
+                            "solver working set > L2",
+                      "parallelism": f"{world} independent k-points (one per GPU)"},
+           "time_to_10_bands_s": eig_ms / args.steps / 1e3,
+           "max_residual": resid,
+           "applies_per_step": applies / max(1, world) / args.steps,
+           "complex128_applies_per_step": applies64 / args.steps,
+           "gpu_launches": launches,
+           "clocks": clk,
+           "roofline": rl,
+           "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                           "GBps": v["bytes"] / max(v["total_ms"], 1e-9) / 1e6}
+                       for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])},
+           "e2e": {"value": e2e_applies / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": int(3 * ctx.N * 8),
+                   "d2h_bytes_per_step": int(NEV * 8 + 3 * ctx.N * 8)},
+           "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -90,6 +90,7 @@ typedef struct {
     long long applies_c64;  /* single-vector A_r applies, complex64                    */
     long long applies_c128; /* single-vector A_r applies, complex128                   */
     double max_residual;    /* max_j ||A_r y_j - lambda_j y_j|| / lambda_j (FP64 apply) */
+    double rr_host_ms;      /* host time spent in the small dense Rayleigh-Ritz solves  */
 } fame_solve_stats;
 
 /*
@@ -225,6 +226,24 @@ FAME_API fame_status fame_grad_eps(fame_ctx* ctx, int nev, const double* dobj_dl
 FAME_API fame_status fame_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol,
                               int max_iter, int flags, double* lambda_out, int* iters_out,
                               void* stream);
+
+/*
+ * Per-kernel timing.  fame_profile(1) clears the records and starts timing:
+ * every kernel launch is then bracketed by two CUDA events recorded on the
+ * stream it is launched on, with the algorithmic bytes (compulsory reads and
+ * writes of that launch) and flops attached.  fame_profile(0) stops.
+ * fame_profile_read synchronises the device and writes up to max entries,
+ * one per kernel kind that launched, returning how many it wrote.
+ */
+typedef struct {
+    char name[32];        /* kernel kind, e.g. "xy_c64"                          */
+    long long launches;
+    double total_ms;      /* sum of event-timed durations                        */
+    double bytes;         /* sum of algorithmic bytes over the launches          */
+    double flops;         /* sum of algorithmic flops over the launches          */
+} fame_kernel_stat;
+FAME_API fame_status fame_profile(int enable);
+FAME_API int fame_profile_read(fame_kernel_stat* out, int max);
 
 /* fame_last_error -- message of the last failure on ctx (or of fame_create if ctx is NULL). */
 FAME_API const char* fame_last_error(const fame_ctx* ctx);

@@ -297,6 +297,7 @@ void fame_destroy(fame_ctx* c) {
     free_tables(c);
     if (c->work.p) cudaFree(c->work.p);
     if (c->solver.p) cudaFree(c->solver.p);
+    if (c->solver2.p) cudaFree(c->solver2.p);
     if (c->partial.p) cudaFree(c->partial.p);
     if (c->Y) cudaFree(c->Y);
     delete c;

@@ -25,9 +25,10 @@ template <typename C> struct RealOf;
 template <> struct RealOf<float2> { using T = float; };
 template <> struct RealOf<double2> { using T = double; };
 
-// G (column-major ku x kv, double2, device) = U^H V
-template <typename C>
-fame_status gram(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V, size_t ld, double2* G,
+// G (column-major ku x kv, double2, device) = U^H V; FP64 products when either side is
+// complex128, else FP32 products with FP64 accumulation
+template <typename CU, typename CV>
+fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, size_t ld, double2* G,
                  cudaStream_t st);
 // out1 = S M[:, :m], out2 = S[:, i0:] M[i0:, :m]  (either output may be null)
 template <typename C, typename Co>
@@ -38,6 +39,17 @@ template <typename C>
 fame_status residual(fame_ctx* c, const C* X, const C* AX, const double* theta_dev,
                      const typename RealOf<C>::T* tinv, int m, C* W, double* part, int nblk,
                      cudaStream_t st);
+// refinement: R = AX - X theta from complex128 X, AX (FP64), W = tinv .* R as complex64
+fame_status residual_mixed(fame_ctx* c, const double2* X, const double2* AX, const double* theta_dev,
+                           int m, float2* W, double* part, int nblk, cudaStream_t st);
+// refinement update: Xn = X M[:m] (FP64) + Q M[m:] (FP32), X32n = complex64 copy of Xn,
+// Pn = Q M[m:] (may be null)
+fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<float2>& Q, size_t ld,
+                          const double2* M, double2* Xn, float2* X32n, float2* Pn, cudaStream_t st);
+// Q <- Q - X cfs (cfs m x nq), in place; FP64 arithmetic when X is complex128
+template <typename CX, typename CQ>
+fame_status orth_against(fame_ctx* c, const CX* X, int m, const BlockList<CQ>& Q, size_t ld,
+                         const double2* cfs, cudaStream_t st);
 template <typename Ci, typename Co>
 fame_status convert(fame_ctx* c, const Ci* in, Co* out, size_t N, cudaStream_t st);
 template <typename C>

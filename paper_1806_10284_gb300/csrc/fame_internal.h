@@ -127,8 +127,10 @@ struct fame_ctx {
     double* Y = nullptr;           // device [nev][2][n] complex128 eigenvectors
     int Y_nev = 0;
     GrowBuf solver;                // solver blocks
+    GrowBuf solver2;               // complex128 blocks of the fallback phase (on demand)
     GrowBuf partial;               // Gram partial sums
     fame_solve_stats stats{};
+    double stats_rr_ms = 0.0;
     std::string err;
 };
 
@@ -144,6 +146,24 @@ fame_status set_err(fame_ctx* c, fame_status s, const std::string& msg);
 
 fame_status grow(fame_ctx* c, GrowBuf& b, size_t bytes);
 void count_launch(int k = 1);
+
+// kernel kinds for the opt-in profiler (profile.cpp)
+enum KernelKind { K_ZIN, K_XY, K_ZOUT, K_YPASS, K_XPASS, K_GRAM, K_GRAM_RED, K_COMBINE, K_RESID,
+                  K_CONVERT, K_GRAD, K_SETUP, K_COUNT };
+// Brackets a launch with events on its stream when profiling is on; attaches the
+// launch's algorithmic bytes and flops.
+class ProfScope {
+  public:
+    ProfScope(int kind, bool dbl, cudaStream_t st, double bytes, double flops = 0.0);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+  private:
+    int id_;
+    cudaStream_t st_;
+    double bytes_, flops_;
+    cudaEvent_t ev_;
+};
 
 // tables (plan.cpp / tables.cu)
 fame_status build_tables(fame_ctx* c);      // twiddles, twist fractions, preconditioner

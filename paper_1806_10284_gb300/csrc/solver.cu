@@ -4,18 +4,27 @@
 // this library uses the block form, whose only operator access is a block of
 // A_r applies, so every FFT pass runs on m vectors at once.
 //
-// Per iteration, on the GPU: R = AX - X Theta and W = T R with the
-// preconditioner T = Sigma_r^{-2} / mean(B^{-1}) (exact for constant B);
-// AW = A_r W; the Gram matrices [X W P]^H [X W P] and [X W P]^H [AX AW AP]
-// accumulated in FP64; on the host: the FP64 Rayleigh-Ritz problem on the
-// GB-orthonormal basis; on the GPU: X <- S C, P <- S_{WP} C_{WP} and the
-// same combinations of AS, so each iteration needs one block apply.
+// One iteration: R = AX - X Theta and W = T R with T = Sigma_r^{-2} / mean(B^{-1})
+// (exact for constant B); AW = A_r W for the columns not yet converged (soft
+// locking of the leading converged ones); Gram matrices of [X W P] against
+// [X W P | AX AW AP] accumulated in FP64; the FP64 Rayleigh-Ritz problem on a
+// GB-orthonormal basis (host); X <- S C, P <- S_{WP} C_{WP} and the same
+// combinations of AS, so an iteration costs one block apply.
 //
-// FAME_MIXED runs this on complex64 blocks until the residual reaches the
-// complex64 floor, then continues on complex128 blocks (refinement) until
-// ||A_r y - lambda y|| <= tol lambda with complex128 applies; FAME_FP64 uses
-// complex128 blocks throughout.
+// FAME_MIXED:
+//   phase 1  complex64 blocks throughout until the residual reaches the
+//            complex64 floor;
+//   phase 2  refinement: X and AX held in complex128 and updated in FP64 from
+//            the complex64 search directions W, P (whose coefficients shrink
+//            with the residual).  The Gram matrices are formed from complex64
+//            copies; their X-X blocks are the identity and Theta of the
+//            previous Rayleigh-Ritz step.  A complex128 apply starts the phase
+//            and confirms convergence.
+//   end      explicit FP64 Rayleigh-Ritz on X with a complex128 apply; the
+//            reported residuals ||A_r y - lambda y|| / lambda come from it.
+// FAME_FP64: complex128 blocks throughout, explicit FP64 Gram matrices.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -26,50 +35,14 @@ namespace {
 
 constexpr int kResidBlocks = 256;
 
-template <typename C>
-struct Workspace {
-    // two copies of S = [X W P] and AS = [AX AW AP], each 3m columns
-    C* S[2];
-    C* AS[2];
-    double2* G;       // [k][2k]
-    double2* Cd;      // [k][m]
-    double* theta;    // [m]
-    double* part;     // [m][kResidBlocks]
-};
-
-template <typename C>
-size_t ws_bytes(size_t ld, int m) {
-    const int k = 3 * m;
-    return 4 * (size_t)k * ld * sizeof(C) + (size_t)k * 2 * k * sizeof(double2) +
-           (size_t)k * m * sizeof(double2) + m * sizeof(double) + (size_t)m * kResidBlocks * sizeof(double) +
-           16 * 256;   // each of the 12 carve-outs below rounds up to 256 bytes
+// per-iteration log on stderr when the environment sets FAME_LOG=1
+bool log_on() {
+    static const bool on = [] {
+        const char* v = std::getenv("FAME_LOG");
+        return v && v[0] == '1';
+    }();
+    return on;
 }
-
-template <typename C>
-Workspace<C> ws_carve(void* base, size_t ld, int m) {
-    const int k = 3 * m;
-    char* p = static_cast<char*>(base);
-    auto take = [&](size_t bytes) {
-        char* r = p;
-        p += (bytes + 255) & ~(size_t)255;
-        return r;
-    };
-    Workspace<C> w;
-    for (int i = 0; i < 2; ++i) {
-        w.S[i] = reinterpret_cast<C*>(take((size_t)k * ld * sizeof(C)));
-        w.AS[i] = reinterpret_cast<C*>(take((size_t)k * ld * sizeof(C)));
-    }
-    w.G = reinterpret_cast<double2*>(take((size_t)k * 2 * k * sizeof(double2)));
-    w.Cd = reinterpret_cast<double2*>(take((size_t)k * m * sizeof(double2)));
-    w.theta = reinterpret_cast<double*>(take(m * sizeof(double)));
-    w.part = reinterpret_cast<double*>(take((size_t)m * kResidBlocks * sizeof(double)));
-    return w;
-}
-
-template <typename R>
-const R* tinv_of(const fame_ctx* c);
-template <> const float* tinv_of<float>(const fame_ctx* c) { return c->tf.tinv; }
-template <> const double* tinv_of<double>(const fame_ctx* c) { return c->td.tinv; }
 
 template <typename C>
 fame_status apply_block(fame_ctx* c, const C* y, C* Ay, int m, cudaStream_t st);
@@ -84,7 +57,48 @@ fame_status apply_block<double2>(fame_ctx* c, const double2* y, double2* Ay, int
     return run_apply<double>(c, y, Ay, m, st);
 }
 
-// Result of one phase.
+template <typename R>
+const R* tinv_of(const fame_ctx* c);
+template <> const float* tinv_of<float>(const fame_ctx* c) { return c->tf.tinv; }
+template <> const double* tinv_of<double>(const fame_ctx* c) { return c->td.tinv; }
+
+// Carves one device allocation into 256-byte aligned pieces.
+struct Carver {
+    char* p;
+    size_t used = 0;
+    explicit Carver(void* base) : p(static_cast<char*>(base)) {}
+    template <typename T>
+    T* take(size_t count) {
+        T* r = reinterpret_cast<T*>(p + used);
+        used += (count * sizeof(T) + 255) & ~(size_t)255;
+        return r;
+    }
+};
+
+// Small device/host buffers shared by the phases.
+struct Small {
+    double2* G;      // [k][2k]
+    double2* Cd;     // [k][m]
+    double* theta;   // [m]
+    double* part;    // [m][kResidBlocks]
+};
+
+size_t small_bytes(int m) {
+    const int k = 3 * m;
+    return ((size_t)k * 2 * k * sizeof(double2) + 255) + ((size_t)k * m * sizeof(double2) + 255) +
+           (m * sizeof(double) + 255) + ((size_t)m * kResidBlocks * sizeof(double) + 255);
+}
+
+Small carve_small(Carver& cv, int m) {
+    const int k = 3 * m;
+    Small s;
+    s.G = cv.take<double2>((size_t)k * 2 * k);
+    s.Cd = cv.take<double2>((size_t)k * m);
+    s.theta = cv.take<double>(m);
+    s.part = cv.take<double>((size_t)m * kResidBlocks);
+    return s;
+}
+
 struct PhaseOut {
     int iters = 0;
     bool converged = false;
@@ -92,102 +106,350 @@ struct PhaseOut {
     std::vector<double> res;
 };
 
-// LOBPCG on blocks of type C, starting from the m columns already in w.S[0][X]
-// (masked).  Stops when the first nev residuals are <= tol, or after max_iter,
-// or (stall_check) when the largest of them has not improved by 10% over
-// 8 iterations.
+// Host Rayleigh-Ritz on the device Gram buffer G = [GB | GA] (each k x k).
+// If implicit_xx > 0 the leading implicit_xx x implicit_xx blocks are replaced by
+// the identity (GB) and diag(theta_prev) (GA).
+int host_rr(fame_ctx* c, const Small& sm, int k, int m, int implicit_xx, const std::vector<double>& theta_prev,
+            double drop, std::vector<double>& theta, std::vector<double2>& Cm, cudaStream_t st, fame_status* err) {
+    std::vector<double2> G((size_t)2 * k * k);
+    cudaError_t e = cudaMemcpyAsync(G.data(), sm.G, G.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *err = set_err(c, FAME_E_CUDA, std::string("Gram readback: ") + cudaGetErrorString(e));
+        return -1;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<double> GB(2 * (size_t)k * k), GA(2 * (size_t)k * k);
+    std::memcpy(GB.data(), G.data(), GB.size() * sizeof(double));
+    std::memcpy(GA.data(), G.data() + (size_t)k * k, GA.size() * sizeof(double));
+    // Hermitise from the lower triangle: entry (i > j) is [W P]^H [AX ...] against the
+    // leading X columns, i.e. built from the accurate AX rather than from AW.
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < j; ++i) {
+            const size_t up = 2 * ((size_t)j * k + i), lo = 2 * ((size_t)i * k + j);
+            GA[up] = GA[lo];
+            GA[up + 1] = -GA[lo + 1];
+            GB[up] = GB[lo];
+            GB[up + 1] = -GB[lo + 1];
+        }
+    for (int j = 0; j < implicit_xx; ++j)
+        for (int i = 0; i < implicit_xx; ++i) {
+            const size_t o = 2 * ((size_t)j * k + i);
+            GB[o] = (i == j) ? 1.0 : 0.0;
+            GB[o + 1] = 0.0;
+            GA[o] = (i == j) ? theta_prev[i] : 0.0;
+            GA[o + 1] = 0.0;
+        }
+    Cm.assign((size_t)k * m, make_double2(0, 0));
+    theta.assign(m, 0.0);
+    const int got = rayleigh_ritz(k, GA.data(), GB.data(), m, drop, theta.data(),
+                                  reinterpret_cast<double*>(Cm.data()));
+    c->stats_rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *err = FAME_OK;
+    return got;
+}
+
+// Refinement Rayleigh-Ritz.  The basis is [X W P] with X the complex128 Ritz
+// block of the previous step (X^H X = I, X^H A X = Theta) and Q = [W P] (nq
+// complex64 columns).  Device G holds, in order: Q^H Q (nq x nq), Q^H AQ
+// (nq x nq), and [X AX]^H Q (2m x nq, FP64 products).  The coupling blocks
+// use A X (complex128) rather than A Q.
+int host_rr_refine(fame_ctx* c, const Small& sm, int m, int nq, const std::vector<double>& theta_prev,
+                   double drop, std::vector<double>& theta, std::vector<double2>& Cm, cudaStream_t st,
+                   fame_status* err) {
+    const size_t cnt = (size_t)2 * nq * nq + (size_t)2 * m * nq;
+    std::vector<double2> G(cnt);
+    cudaError_t e = cudaMemcpyAsync(G.data(), sm.G, cnt * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *err = set_err(c, FAME_E_CUDA, std::string("Gram readback: ") + cudaGetErrorString(e));
+        return -1;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const int k = m + nq;
+    const double2* QQ = G.data();
+    const double2* QAQ = QQ + (size_t)nq * nq;
+    const double2* XQ = QAQ + (size_t)nq * nq;    // (2m) x nq, column-major
+    std::vector<double> GB(2 * (size_t)k * k, 0.0), GA(2 * (size_t)k * k, 0.0);
+    auto set = [&](std::vector<double>& M, int i, int j, double re, double im) {
+        M[2 * ((size_t)j * k + i)] = re;
+        M[2 * ((size_t)j * k + i) + 1] = im;
+    };
+    for (int i = 0; i < m; ++i) {
+        set(GB, i, i, 1.0, 0.0);
+        set(GA, i, i, theta_prev[i], 0.0);
+    }
+    for (int q = 0; q < nq; ++q) {
+        for (int i = 0; i < m; ++i) {
+            const double2 xb = XQ[(size_t)q * 2 * m + i];       // X_i^H Q_q
+            const double2 xa = XQ[(size_t)q * 2 * m + m + i];   // (A X_i)^H Q_q
+            set(GB, m + q, i, xb.x, -xb.y);
+            set(GA, m + q, i, xa.x, -xa.y);
+        }
+        for (int p = 0; p < nq; ++p) {
+            const double2 b = QQ[(size_t)q * nq + p], a = QAQ[(size_t)q * nq + p];
+            set(GB, m + p, m + q, b.x, b.y);
+            set(GA, m + p, m + q, a.x, a.y);
+        }
+    }
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < j; ++i) {
+            const size_t up = 2 * ((size_t)j * k + i), lo = 2 * ((size_t)i * k + j);
+            GA[up] = GA[lo];
+            GA[up + 1] = -GA[lo + 1];
+            GB[up] = GB[lo];
+            GB[up + 1] = -GB[lo + 1];
+        }
+    Cm.assign((size_t)k * m, make_double2(0, 0));
+    theta.assign(m, 0.0);
+    const int got = rayleigh_ritz(k, GA.data(), GB.data(), m, drop, theta.data(),
+                                  reinterpret_cast<double*>(Cm.data()));
+    c->stats_rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *err = FAME_OK;
+    return got;
+}
+
+fame_status upload_rr(fame_ctx* c, const Small& sm, const std::vector<double2>& Cm,
+                      const std::vector<double>& theta, cudaStream_t st) {
+    FAME_CUDA_TRY(c, cudaMemcpyAsync(sm.Cd, Cm.data(), Cm.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    FAME_CUDA_TRY(c, cudaMemcpyAsync(sm.theta, theta.data(), theta.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    return FAME_OK;
+}
+
+fame_status read_norms(fame_ctx* c, const Small& sm, int m, const std::vector<double>& theta,
+                       std::vector<double>& res, cudaStream_t st) {
+    std::vector<double> part((size_t)m * kResidBlocks);
+    FAME_CUDA_TRY(c, cudaMemcpyAsync(part.data(), sm.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FAME_CUDA_TRY(c, cudaStreamSynchronize(st));
+    res.assign(m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        double ss = 0.0;
+        for (int b = 0; b < kResidBlocks; ++b) ss += part[(size_t)j * kResidBlocks + b];
+        res[j] = std::sqrt(ss) / std::fabs(theta[j]);
+    }
+    return FAME_OK;
+}
+
+int leading_converged(const std::vector<double>& res, int nev, double tol) {
+    int j0 = 0;
+    while (j0 < nev && res[j0] <= tol) ++j0;
+    return j0;
+}
+
+// ---------------------------------------------------------------------------
+// LOBPCG with explicit Gram matrices on blocks of type C.  X starts in S[0]
+// (first m columns).  Result left in S[0] / AS[0].
+// ---------------------------------------------------------------------------
 template <typename C>
-fame_status lobpcg(fame_ctx* c, Workspace<C>& w, int m, int nev, double tol, int max_iter,
-                   bool stall_check, double drop, cudaStream_t st, PhaseOut& out) {
+fame_status lob_explicit(fame_ctx* c, C* const S[2], C* const AS[2], const Small& sm, int m, int nev,
+                         double tol, int max_iter, bool stall_check, double drop, cudaStream_t st,
+                         PhaseOut& out) {
     using R = typename RealOf<C>::T;
-    const size_t n = (size_t)c->n, ld = 2 * n;
+    const size_t ld = 2 * (size_t)c->n;
     const R* tinv = tinv_of<R>(c);
-    int cur = 0;
-    int np = 0;       // columns of P
-    int nw = 0;       // columns of W
+    int cur = 0, np = 0, nw = 0, j0 = 0;
     fame_status s;
-    std::vector<double2> G, Cm;
-    std::vector<double> theta(m), part((size_t)m * kResidBlocks), res(m, 1e300);
-    std::vector<double> best_hist;
-    // initial Rayleigh-Ritz on X
-    C* X = w.S[cur];
-    C* AX = w.AS[cur];
-    if ((s = apply_block<C>(c, X, AX, m, st)) != FAME_OK) return s;
+    std::vector<double> theta(m, 0.0), res(m, 1e300), hist;
+    std::vector<double2> Cm;
+    if ((s = apply_block<C>(c, S[0], AS[0], m, st)) != FAME_OK) return s;
     for (int it = 0; it <= max_iter; ++it) {
-        X = w.S[cur];
-        AX = w.AS[cur];
-        C* Wb = X + (size_t)m * ld;
-        C* AWb = AX + (size_t)m * ld;
+        C* X = S[cur];
+        C* AX = AS[cur];
+        C* Wb = X + (size_t)m * ld + (size_t)j0 * ld;
+        C* AWb = AX + (size_t)m * ld + (size_t)j0 * ld;
         C* Pb = X + (size_t)2 * m * ld;
         C* APb = AX + (size_t)2 * m * ld;
         const int k = m + nw + np;
-        BlockList<C> U = blocks<C>(X, m, Wb, nw, Pb, np);
-        BlockList<C> V;
-        // G = [X W P]^H [X W P | AX AW AP]: two Gram launches into one k x 2k buffer
-        s = gram<C>(c, U, U, ld, w.G, st);
-        if (s != FAME_OK) return s;
-        V = blocks<C>(AX, m, AWb, nw, APb, np);
-        s = gram<C>(c, U, V, ld, w.G + (size_t)k * k, st);
-        if (s != FAME_OK) return s;
-        G.resize((size_t)2 * k * k);
-        FAME_CUDA_TRY(c, cudaMemcpyAsync(G.data(), w.G, G.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
-        FAME_CUDA_TRY(c, cudaStreamSynchronize(st));
-        std::vector<double> GB(2 * (size_t)k * k), GA(2 * (size_t)k * k);
-        std::memcpy(GB.data(), G.data(), GB.size() * sizeof(double));
-        std::memcpy(GA.data(), G.data() + (size_t)k * k, GA.size() * sizeof(double));
-        Cm.assign((size_t)k * m, make_double2(0, 0));
-        const int got = rayleigh_ritz(k, GA.data(), GB.data(), m, drop, theta.data(),
-                                      reinterpret_cast<double*>(Cm.data()));
+        const BlockList<C> U = blocks<C>(X, m, Wb, nw, Pb, np);
+        const BlockList<C> V = blocks<C>(AX, m, AWb, nw, APb, np);
+        if ((s = gram<C, C>(c, U, U, ld, sm.G, st)) != FAME_OK) return s;
+        if ((s = gram<C, C>(c, U, V, ld, sm.G + (size_t)k * k, st)) != FAME_OK) return s;
+        std::vector<double> th;
+        const int got = host_rr(c, sm, k, m, 0, theta, drop, th, Cm, st, &s);
+        if (got < 0) return s;
         if (got < m) {
-            // basis lost rank: restart the search directions from X alone
             if (np == 0 && nw == 0) return set_err(c, FAME_E_NOCONV, "block lost rank");
-            np = 0;
-            nw = 0;
+            np = nw = 0;
             continue;
         }
-        FAME_CUDA_TRY(c, cudaMemcpyAsync(w.Cd, Cm.data(), Cm.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-        FAME_CUDA_TRY(c, cudaMemcpyAsync(w.theta, theta.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
-        // X' = S C, P' = S[m:] C[m:]   (and the same for AS) into the other buffers
+        theta = th;
+        if ((s = upload_rr(c, sm, Cm, theta, st)) != FAME_OK) return s;
         const int nxt = cur ^ 1;
-        C* Xn = w.S[nxt];
-        C* AXn = w.AS[nxt];
         const bool have_p = (nw + np) > 0;
-        if ((s = combine<C, C>(c, U, ld, w.Cd, m, m, Xn, have_p ? Xn + (size_t)2 * m * ld : nullptr, st)) != FAME_OK) return s;
-        if ((s = combine<C, C>(c, V, ld, w.Cd, m, m, AXn, have_p ? AXn + (size_t)2 * m * ld : nullptr, st)) != FAME_OK) return s;
+        if ((s = combine<C, C>(c, U, ld, sm.Cd, m, m, S[nxt], have_p ? S[nxt] + (size_t)2 * m * ld : nullptr, st)) != FAME_OK) return s;
+        if ((s = combine<C, C>(c, V, ld, sm.Cd, m, m, AS[nxt], have_p ? AS[nxt] + (size_t)2 * m * ld : nullptr, st)) != FAME_OK) return s;
         np = have_p ? m : 0;
         cur = nxt;
-        X = Xn;
-        AX = AXn;
-        Wb = X + (size_t)m * ld;
-        AWb = AX + (size_t)m * ld;
-        // residuals and preconditioned directions
-        if ((s = residual<C>(c, X, AX, w.theta, tinv, m, Wb, w.part, kResidBlocks, st)) != FAME_OK) return s;
-        FAME_CUDA_TRY(c, cudaMemcpyAsync(part.data(), w.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-        FAME_CUDA_TRY(c, cudaStreamSynchronize(st));
+        X = S[cur];
+        AX = AS[cur];
+        if ((s = residual<C>(c, X, AX, sm.theta, tinv, m, X + (size_t)m * ld, sm.part, kResidBlocks, st)) != FAME_OK) return s;
+        if ((s = read_norms(c, sm, m, theta, res, st)) != FAME_OK) return s;
         double worst = 0.0;
-        for (int j = 0; j < m; ++j) {
-            double ss = 0.0;
-            for (int b = 0; b < kResidBlocks; ++b) ss += part[(size_t)j * kResidBlocks + b];
-            res[j] = std::sqrt(ss) / std::fabs(theta[j]);
-            if (j < nev) worst = std::max(worst, res[j]);
-        }
+        for (int j = 0; j < nev; ++j) worst = std::max(worst, res[j]);
         out.iters = it + 1;
-        out.theta.assign(theta.begin(), theta.end());
-        out.res.assign(res.begin(), res.end());
+        out.theta = theta;
+        out.res = res;
+        if (log_on())
+            std::fprintf(stderr, "[fame] %s it %d k %d worst %.3e theta0 %.10g theta%d %.10g\n",
+                         sizeof(C) == 8 ? "c64" : "c128", it, k, worst, theta[0], nev - 1, theta[nev - 1]);
         if (worst <= tol) { out.converged = true; break; }
         if (stall_check) {
-            best_hist.push_back(worst);
-            const size_t h = best_hist.size();
-            if (h > 8 && worst > 0.9 * best_hist[h - 9]) break;
+            // the complex64 floor: after 20 iterations, no 30% gain over the last 10
+            hist.push_back(worst);
+            const size_t h = hist.size();
+            if (h > 20 && worst < 1e-3) {
+                double best_old = *std::min_element(hist.begin(), hist.end() - 10);
+                if (worst > 0.7 * best_old) break;
+            }
         }
         if (it == max_iter) break;
-        nw = m;
-        if ((s = apply_block<C>(c, Wb, AWb, nw, st)) != FAME_OK) return s;
+        j0 = leading_converged(res, nev, tol);
+        nw = m - j0;
+        {
+            // ortho-LOBPCG (Hetmaniuk and Lehoucq 2006): W and P orthogonalised against X
+            // (AP alongside), then AW for the orthogonalised W
+            C* Wn = X + (size_t)m * ld + (size_t)j0 * ld;
+            C* Pn = X + (size_t)2 * m * ld;
+            C* APn = AX + (size_t)2 * m * ld;
+            const BlockList<C> Q = blocks<C>(Wn, nw, Pn, np);
+            const BlockList<C> Xl = blocks<C>(X, m);
+            if ((s = gram<C, C>(c, Xl, Q, ld, sm.G, st)) != FAME_OK) return s;
+            if ((s = orth_against<C, C>(c, X, m, Q, ld, sm.G, st)) != FAME_OK) return s;
+            if (np > 0 && (s = orth_against<C, C>(c, AX, m, blocks<C>(APn, np), ld, sm.G + (size_t)m * nw, st)) != FAME_OK) return s;
+            if ((s = apply_block<C>(c, Wn, AX + (size_t)m * ld + (size_t)j0 * ld, nw, st)) != FAME_OK) return s;
+        }
     }
-    // leave the result in w.S[0] / w.AS[0]
     if (cur != 0) {
-        FAME_CUDA_TRY(c, cudaMemcpyAsync(w.S[0], w.S[cur], (size_t)m * ld * sizeof(C), cudaMemcpyDeviceToDevice, st));
-        FAME_CUDA_TRY(c, cudaMemcpyAsync(w.AS[0], w.AS[cur], (size_t)m * ld * sizeof(C), cudaMemcpyDeviceToDevice, st));
+        FAME_CUDA_TRY(c, cudaMemcpyAsync(S[0], S[cur], (size_t)m * ld * sizeof(C), cudaMemcpyDeviceToDevice, st));
+        FAME_CUDA_TRY(c, cudaMemcpyAsync(AS[0], AS[cur], (size_t)m * ld * sizeof(C), cudaMemcpyDeviceToDevice, st));
+    }
+    return FAME_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Explicit FP64 Rayleigh-Ritz of the complex128 block X (m columns) with a
+// complex128 apply: X <- X C, AX <- (A X) C; residual norms from them.
+// X, AX in buffers a/aa; results in b/ab.
+// ---------------------------------------------------------------------------
+fame_status rr64(fame_ctx* c, double2* a, double2* aa, double2* b, double2* ab, const Small& sm, int m,
+                 bool do_apply, std::vector<double>& theta, std::vector<double>& res, cudaStream_t st) {
+    const size_t ld = 2 * (size_t)c->n;
+    fame_status s;
+    if (do_apply && (s = apply_block<double2>(c, a, aa, m, st)) != FAME_OK) return s;
+    const BlockList<double2> U = blocks<double2>(a, m), V = blocks<double2>(aa, m);
+    if ((s = gram<double2, double2>(c, U, U, ld, sm.G, st)) != FAME_OK) return s;
+    if ((s = gram<double2, double2>(c, U, V, ld, sm.G + (size_t)m * m, st)) != FAME_OK) return s;
+    std::vector<double2> Cm;
+    std::vector<double> th;
+    const int got = host_rr(c, sm, m, m, 0, theta, 1e-14, th, Cm, st, &s);
+    if (got < 0) return s;
+    if (got < m) return set_err(c, FAME_E_NOCONV, "refined block lost rank");
+    theta = th;
+    if ((s = upload_rr(c, sm, Cm, theta, st)) != FAME_OK) return s;
+    if ((s = combine<double2, double2>(c, U, ld, sm.Cd, m, m, b, nullptr, st)) != FAME_OK) return s;
+    if ((s = combine<double2, double2>(c, V, ld, sm.Cd, m, m, ab, nullptr, st)) != FAME_OK) return s;
+    if ((s = residual<double2>(c, b, ab, sm.theta, c->td.tinv, m, nullptr, sm.part, kResidBlocks, st)) != FAME_OK) return s;
+    return read_norms(c, sm, m, theta, res, st);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed refinement.  X32 (complex64 copy of X) starts in S32[0]; on return the
+// refined complex128 X is in X64[0] with AX in AX64[0].
+// ---------------------------------------------------------------------------
+fame_status lob_refine(fame_ctx* c, float2* const S[2], float2* const AS[2], double2* const X64[2],
+                       double2* const AX64[2], const Small& sm, int m, int nev, double tol, int max_iter,
+                       cudaStream_t st, PhaseOut& out) {
+    const size_t ld = 2 * (size_t)c->n;
+    fame_status s;
+    std::vector<double> theta(m, 0.0), res;
+    // start: promote X, complex128 apply, explicit FP64 Rayleigh-Ritz
+    if ((s = convert<float2, double2>(c, S[0], X64[1], (size_t)m * ld, st)) != FAME_OK) return s;
+    if ((s = rr64(c, X64[1], AX64[1], X64[0], AX64[0], sm, m, true, theta, res, st)) != FAME_OK) return s;
+    int cur = 0, np = 0, nw = 0, j0 = 0;
+    // complex64 copies of X, AX in the X slots of S[0], AS[0]
+    if ((s = convert<double2, float2>(c, X64[0], S[0], (size_t)m * ld, st)) != FAME_OK) return s;
+    if ((s = convert<double2, float2>(c, AX64[0], AS[0], (size_t)m * ld, st)) != FAME_OK) return s;
+    std::vector<double2> Cm;
+    std::vector<double> hist;
+    for (int it = 0; it <= max_iter; ++it) {
+        // residuals of the tracked pair; W for every column
+        float2* X32 = S[cur];
+        float2* AX32 = AS[cur];
+        if ((s = residual_mixed(c, X64[cur], AX64[cur], sm.theta, m, X32 + (size_t)m * ld, sm.part, kResidBlocks, st)) != FAME_OK) return s;
+        if ((s = read_norms(c, sm, m, theta, res, st)) != FAME_OK) return s;
+        double worst = 0.0;
+        for (int j = 0; j < nev; ++j) worst = std::max(worst, res[j]);
+        out.iters = it;
+        if (log_on())
+            std::fprintf(stderr, "[fame] refine it %d np %d worst %.3e theta0 %.14g\n", it, np, worst, theta[0]);
+        hist.push_back(worst);
+        if (hist.size() > 8 && worst > 0.5 * *std::min_element(hist.begin(), hist.end() - 4)) {
+            // no factor-2 gain over the last 4 iterations: the complex64 directions no
+            // longer resolve the residual; hand over to the complex128 solver
+            out.theta = theta;
+            out.res = res;
+            break;
+        }
+        if (worst <= 0.5 * tol) {
+            // confirm with a complex128 apply and an explicit FP64 Rayleigh-Ritz
+            std::vector<double> th2 = theta, r2;
+            if ((s = rr64(c, X64[cur], AX64[cur ^ 1], X64[cur ^ 1], AX64[cur], sm, m, true, th2, r2, st)) != FAME_OK) return s;
+            // rr64 left X in X64[cur^1], AX in AX64[cur]: move X back
+            FAME_CUDA_TRY(c, cudaMemcpyAsync(X64[cur], X64[cur ^ 1], (size_t)m * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            theta = th2;
+            res = r2;
+            worst = 0.0;
+            for (int j = 0; j < nev; ++j) worst = std::max(worst, res[j]);
+            out.theta = theta;
+            out.res = res;
+            if (worst <= tol) { out.converged = true; break; }
+            if ((s = convert<double2, float2>(c, X64[cur], X32, (size_t)m * ld, st)) != FAME_OK) return s;
+            if ((s = convert<double2, float2>(c, AX64[cur], AX32, (size_t)m * ld, st)) != FAME_OK) return s;
+            if ((s = residual_mixed(c, X64[cur], AX64[cur], sm.theta, m, X32 + (size_t)m * ld, sm.part, kResidBlocks, st)) != FAME_OK) return s;
+            np = 0;
+        }
+        out.theta = theta;
+        out.res = res;
+        if (it == max_iter) break;
+        j0 = leading_converged(res, nev, 0.5 * tol);
+        nw = m - j0;
+        float2* Wb = X32 + (size_t)m * ld + (size_t)j0 * ld;
+        float2* AWb = AX32 + (size_t)m * ld + (size_t)j0 * ld;
+        float2* Pb = X32 + (size_t)2 * m * ld;
+        float2* APb = AX32 + (size_t)2 * m * ld;
+        const int nq = nw + np;
+        const BlockList<float2> Q = blocks<float2>(Wb, nw, Pb, np);
+        const BlockList<float2> AQ = blocks<float2>(AWb, nw, APb, np);
+        // Orthogonalise the complex64 directions against X in FP64 (c = X^H Q,
+        // Q <- Q - X c, AP <- AP - AX c_P) so that no direction carries a large
+        // component along X whose complex64 rounding the Rayleigh-Ritz step would
+        // amplify; then AW for the orthogonalised W.
+        const BlockList<double2> Xl = blocks<double2>(X64[cur], m);
+        if ((s = gram<double2, float2>(c, Xl, Q, ld, sm.G, st)) != FAME_OK) return s;
+        if ((s = orth_against<double2, float2>(c, X64[cur], m, Q, ld, sm.G, st)) != FAME_OK) return s;
+        if (np > 0 && (s = orth_against<double2, float2>(c, AX64[cur], m, blocks<float2>(APb, np), ld, sm.G + (size_t)m * nw, st)) != FAME_OK) return s;
+        if ((s = apply_block<float2>(c, Wb, AWb, nw, st)) != FAME_OK) return s;
+        // W/P blocks, FP32 products: [W P]^H [W P | AW AP]
+        if ((s = gram<float2, float2>(c, Q, Q, ld, sm.G, st)) != FAME_OK) return s;
+        if ((s = gram<float2, float2>(c, Q, AQ, ld, sm.G + (size_t)nq * nq, st)) != FAME_OK) return s;
+        // X rows, FP64 products on the complex128 X and AX: [X AX]^H [W P]
+        const BlockList<double2> XA = blocks<double2>(X64[cur], m, AX64[cur], m);
+        if ((s = gram<double2, float2>(c, XA, Q, ld, sm.G + (size_t)2 * nq * nq, st)) != FAME_OK) return s;
+        std::vector<double> th;
+        const int got = host_rr_refine(c, sm, m, nq, theta, 1e-6, th, Cm, st, &s);
+        if (got < 0) return s;
+        if (got < m) { np = 0; continue; }
+        theta = th;
+        if ((s = upload_rr(c, sm, Cm, theta, st)) != FAME_OK) return s;
+        const int nxt = cur ^ 1;
+        if ((s = combine_mixed(c, X64[cur], m, Q, ld, sm.Cd, X64[nxt], S[nxt], S[nxt] + (size_t)2 * m * ld, st)) != FAME_OK) return s;
+        if ((s = combine_mixed(c, AX64[cur], m, AQ, ld, sm.Cd, AX64[nxt], AS[nxt], AS[nxt] + (size_t)2 * m * ld, st)) != FAME_OK) return s;
+        np = m;
+        cur = nxt;
+    }
+    if (cur != 0) {
+        FAME_CUDA_TRY(c, cudaMemcpyAsync(X64[0], X64[cur], (size_t)m * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        FAME_CUDA_TRY(c, cudaMemcpyAsync(AX64[0], AX64[cur], (size_t)m * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     }
     return FAME_OK;
 }
@@ -197,43 +459,69 @@ fame_status lobpcg(fame_ctx* c, Workspace<C>& w, int m, int nev, double tol, int
 fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, double* lambda_out,
                      void* Y_out, int* iters_out, cudaStream_t st) {
     const size_t n = (size_t)c->n, ld = 2 * n;
-    const int m = std::min<long long>(nev + std::max(4, (nev + 1) / 2), ld);
+    const int m = (int)std::min<long long>(nev + std::max(4, (nev + 1) / 2), (long long)ld / 3);
     const bool mixed = (flags & FAME_MIXED) && !(flags & FAME_FP64);
     c->stats = fame_solve_stats{};
+    c->stats_rr_ms = 0.0;
     fame_status s;
-    const size_t b32 = mixed ? ws_bytes<float2>(ld, m) : 0;
-    const size_t b64 = ws_bytes<double2>(ld, m);
-    if ((s = grow(c, c->solver, std::max(b32, b64))) != FAME_OK) return s;
+    const int k = 3 * m;
+    size_t bytes = small_bytes(m) + 256;
+    if (mixed)
+        bytes += 4 * (((size_t)k * ld * sizeof(float2) + 255)) + 4 * (((size_t)m * ld * sizeof(double2) + 255));
+    else
+        bytes += 4 * (((size_t)k * ld * sizeof(double2) + 255));
+    if ((s = grow(c, c->solver, bytes)) != FAME_OK) return s;
+    Carver cv(c->solver.p);
+    const Small sm = carve_small(cv, m);
     const uint64_t seed = 0x5eedF00Dull ^ ((uint64_t)c->n << 20) ^ (uint64_t)nev;
-    PhaseOut ph1, ph2;
-    Workspace<double2> w64 = ws_carve<double2>(c->solver.p, ld, m);
     const bool warm = (flags & FAME_WARM_START) && c->Y && c->Y_nev >= 1;
+    const int nwarm = warm ? std::min(c->Y_nev, m) : 0;
+    PhaseOut ph1, ph2;
+    double2* Xfinal = nullptr;
     if (mixed) {
-        Workspace<float2> w32 = ws_carve<float2>(c->solver.p, ld, m);
-        if ((s = random_block<float2>(c, w32.S[0], m, seed, c->tf.tinv, st)) != FAME_OK) return s;
-        if (warm) {
-            const int nw = std::min(c->Y_nev, m);
-            if ((s = convert<double2, float2>(c, reinterpret_cast<const double2*>(c->Y), w32.S[0], (size_t)nw * ld, st)) != FAME_OK) return s;
-        }
-        // complex64 phase: stop at the complex64 floor (stall) or well below tol
+        float2* S[2];
+        float2* AS[2];
+        double2* X64[2];
+        double2* AX64[2];
+        for (int i = 0; i < 2; ++i) { S[i] = cv.take<float2>((size_t)k * ld); AS[i] = cv.take<float2>((size_t)k * ld); }
+        for (int i = 0; i < 2; ++i) { X64[i] = cv.take<double2>((size_t)m * ld); AX64[i] = cv.take<double2>((size_t)m * ld); }
+        if ((s = random_block<float2>(c, S[0], m, seed, c->tf.tinv, st)) != FAME_OK) return s;
+        if (warm && (s = convert<double2, float2>(c, reinterpret_cast<const double2*>(c->Y), S[0], (size_t)nwarm * ld, st)) != FAME_OK) return s;
         const double tol32 = std::max(tol, 2e-5);
-        if ((s = lobpcg<float2>(c, w32, m, nev, tol32, max_iter, true, 1e-6, st, ph1)) != FAME_OK) return s;
+        if ((s = lob_explicit<float2>(c, S, AS, sm, m, nev, tol32, max_iter, true, 1e-6, st, ph1)) != FAME_OK) return s;
         c->stats.iters_mixed = ph1.iters;
-        // promote X to complex128 for refinement (w64.S[0] overlaps w32 buffers: stage through AS[1])
-        float2* stage = reinterpret_cast<float2*>(w64.AS[1]);
-        FAME_CUDA_TRY(c, cudaMemcpyAsync(stage, w32.S[0], (size_t)m * ld * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-        if ((s = convert<float2, double2>(c, stage, w64.S[0], (size_t)m * ld, st)) != FAME_OK) return s;
-    } else {
-        if ((s = random_block<double2>(c, w64.S[0], m, seed, c->td.tinv, st)) != FAME_OK) return s;
-        if (warm) {
-            const int nw = std::min(c->Y_nev, m);
-            FAME_CUDA_TRY(c, cudaMemcpyAsync(w64.S[0], c->Y, (size_t)nw * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        const int left = std::max(2, max_iter - ph1.iters);
+        if ((s = lob_refine(c, S, AS, X64, AX64, sm, m, nev, tol, left, st, ph2)) != FAME_OK) return s;
+        c->stats.iters_fp64 = ph2.iters;
+        Xfinal = X64[0];
+        const int left2 = max_iter - ph1.iters - ph2.iters;
+        if (!ph2.converged && left2 > 0) {
+            // refinement stalled above tol: complex128 blocks from the refined X
+            if ((s = grow(c, c->solver2, 4 * (((size_t)k * ld * sizeof(double2) + 255)) + 256)) != FAME_OK) return s;
+            Carver cv2(c->solver2.p);
+            double2* S2[2];
+            double2* AS2[2];
+            for (int i = 0; i < 2; ++i) { S2[i] = cv2.take<double2>((size_t)k * ld); AS2[i] = cv2.take<double2>((size_t)k * ld); }
+            FAME_CUDA_TRY(c, cudaMemcpyAsync(S2[0], X64[0], (size_t)m * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            PhaseOut ph3;
+            if ((s = lob_explicit<double2>(c, S2, AS2, sm, m, nev, tol, left2, false, 1e-12, st, ph3)) != FAME_OK) return s;
+            c->stats.iters_fp64 += ph3.iters;
+            ph2.iters += ph3.iters;
+            ph2.converged = ph3.converged;
+            ph2.theta = ph3.theta;
+            ph2.res = ph3.res;
+            Xfinal = S2[0];
         }
+    } else {
+        double2* S[2];
+        double2* AS[2];
+        for (int i = 0; i < 2; ++i) { S[i] = cv.take<double2>((size_t)k * ld); AS[i] = cv.take<double2>((size_t)k * ld); }
+        if ((s = random_block<double2>(c, S[0], m, seed, c->td.tinv, st)) != FAME_OK) return s;
+        if (warm) FAME_CUDA_TRY(c, cudaMemcpyAsync(S[0], c->Y, (size_t)nwarm * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        if ((s = lob_explicit<double2>(c, S, AS, sm, m, nev, tol, max_iter, false, 1e-12, st, ph2)) != FAME_OK) return s;
+        c->stats.iters_fp64 = ph2.iters;
+        Xfinal = S[0];
     }
-    const int left = std::max(1, max_iter - ph1.iters);
-    if ((s = lobpcg<double2>(c, w64, m, nev, tol, left, false, 1e-12, st, ph2)) != FAME_OK) return s;
-    c->stats.iters_fp64 = ph2.iters;
-    // keep eigenpairs; lambda from the last Rayleigh-Ritz (complex128 basis)
     c->lambda.assign(ph2.theta.begin(), ph2.theta.begin() + nev);
     double worst = 0.0;
     for (int j = 0; j < nev; ++j) worst = std::max(worst, ph2.res[j]);
@@ -242,16 +530,19 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
         if (c->Y) cudaFree(c->Y);
         c->Y = nullptr;
         c->Y_nev = 0;
-        if (cudaMalloc((void**)&c->Y, (size_t)nev * ld * sizeof(double2)) != cudaSuccess)
+        if (cudaMalloc((void**)&c->Y, (size_t)nev * ld * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
             return set_err(c, FAME_E_NOMEM, "cudaMalloc eigenvectors");
+        }
         c->Y_nev = nev;
     }
-    FAME_CUDA_TRY(c, cudaMemcpyAsync(c->Y, w64.S[0], (size_t)nev * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    FAME_CUDA_TRY(c, cudaMemcpyAsync(c->Y, Xfinal, (size_t)nev * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     if (Y_out)
-        FAME_CUDA_TRY(c, cudaMemcpyAsync(Y_out, w64.S[0], (size_t)nev * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        FAME_CUDA_TRY(c, cudaMemcpyAsync(Y_out, Xfinal, (size_t)nev * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     FAME_CUDA_TRY(c, cudaStreamSynchronize(st));
     for (int j = 0; j < nev; ++j) lambda_out[j] = c->lambda[j];
     if (iters_out) *iters_out = ph1.iters + ph2.iters;
+    c->stats.rr_host_ms = c->stats_rr_ms;
     if (!ph2.converged)
         return set_err(c, FAME_E_NOCONV, "eigensolver reached max_iter; max residual " + std::to_string(worst));
     return FAME_OK;

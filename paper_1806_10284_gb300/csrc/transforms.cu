@@ -619,16 +619,25 @@ ZCfg z_config(const fame_ctx* c, int m) {
 // ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
+// log2 of a grid length, for flop counts (5 N log2 N per complex DFT of length N)
+static double lg2(int L) { return std::log2((double)L); }
+
 template <typename R>
 static fame_status xy_stage(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int m,
                             int mode, R lift_scale, cudaStream_t st) {
     using C = typename cpx<R>::T;
+    const bool dbl = sizeof(R) == 8;
     const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
+    const double nm = (double)c->n * m;
     const size_t plane_smem = (size_t)(n1 + n2 + 2 * n1 * n2) * sizeof(C);
     fame_status s;
     if (plane_smem <= kSmemCap) {
         if ((s = set_smem<R>(c, (const void*)k_xy<R>, plane_smem)) != FAME_OK) return s;
         const int th = (n1 * n2 >= 2048) ? 512 : 256;
+        // reads and writes the 3 m n workspace once, reads B^{-1} (3n) once
+        const double bytes = 2.0 * 3 * nm * sizeof(C) + 3.0 * c->n * sizeof(R);
+        const double flops = 3 * nm * 5.0 * (mode == 0 ? 2.0 : 1.0) * (lg2(n1) + lg2(n2));
+        ProfScope ps(K_XY, dbl, st, bytes, flops);
         k_xy<R><<<(unsigned)(3LL * m * n3), th, plane_smem, st>>>(P, W, mode, lift_scale);
         count_launch();
         FAME_CUDA_TRY(c, cudaGetLastError());
@@ -645,10 +654,19 @@ static fame_status xy_stage(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T
     if ((s = set_smem<R>(c, (const void*)k_xpass<R>, xsm)) != FAME_OK) return s;
     const long long nrows = 3LL * m * n3 * n2;
     dim3 yg((n1 + TPy - 1) / TPy, n3, 3 * m);
-    k_ypass<R><<<yg, 256, ysm, st>>>(P, W, TPy, 0);
-    k_xpass<R><<<(unsigned)((nrows + RPB - 1) / RPB), 256, xsm, st>>>(P, W, nrows, RPB, mode, lift_scale);
+    const double ybytes = 2.0 * 3 * nm * sizeof(C), yflops = 3 * nm * 5.0 * lg2(n2);
+    {
+        ProfScope ps(K_YPASS, dbl, st, ybytes, yflops);
+        k_ypass<R><<<yg, 256, ysm, st>>>(P, W, TPy, 0);
+    }
+    {
+        ProfScope ps(K_XPASS, dbl, st, ybytes + 3.0 * c->n * sizeof(R),
+                     3 * nm * 5.0 * lg2(n1) * (mode == 0 ? 2.0 : 1.0));
+        k_xpass<R><<<(unsigned)((nrows + RPB - 1) / RPB), 256, xsm, st>>>(P, W, nrows, RPB, mode, lift_scale);
+    }
     count_launch(2);
     if (mode == 0) {
+        ProfScope ps(K_YPASS, dbl, st, ybytes, yflops);
         k_ypass<R><<<yg, 256, ysm, st>>>(P, W, TPy, 1);
         count_launch();
     }
@@ -661,7 +679,9 @@ fame_status run_apply(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>:
                       cudaStream_t st) {
     using C = typename cpx<R>::T;
     if (m <= 0) return FAME_OK;
-    const int n1 = c->plan.n[0], n2 = c->plan.n[1];
+    const bool dbl = sizeof(R) == 8;
+    const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
+    const double nm = (double)c->n * m;
     const size_t need = (size_t)m * 3 * (size_t)c->n * sizeof(C);
     fame_status s = grow(c, c->work, need);
     if (s != FAME_OK) return s;
@@ -671,11 +691,18 @@ fame_status run_apply(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>:
     if ((s = set_smem<R>(c, (const void*)k_zin<R>, z.smem)) != FAME_OK) return s;
     if ((s = set_smem<R>(c, (const void*)k_zout<R>, z.smem)) != FAME_OK) return s;
     dim3 grid((n1 + z.TP - 1) / z.TP, n2, (m + z.vpc - 1) / z.vpc);
-    k_zin<R><<<grid, z.threads, z.smem, st>>>(P, y, W, m, z.TP, z.vpc);
+    {
+        // reads y (2 m n), writes the workspace (3 m n)
+        ProfScope ps(K_ZIN, dbl, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
+        k_zin<R><<<grid, z.threads, z.smem, st>>>(P, y, W, m, z.TP, z.vpc);
+    }
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
     if ((s = xy_stage<R>(c, P, W, m, 0, (R)0, st)) != FAME_OK) return s;
-    k_zout<R><<<grid, z.threads, z.smem, st>>>(P, W, Ay, m, z.TP, z.vpc);
+    {
+        ProfScope ps(K_ZOUT, dbl, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
+        k_zout<R><<<grid, z.threads, z.smem, st>>>(P, W, Ay, m, z.TP, z.vpc);
+    }
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
     return FAME_OK;
@@ -684,14 +711,19 @@ fame_status run_apply(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>:
 template <typename R>
 fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* x, int m,
                      cudaStream_t st) {
+    using C = typename cpx<R>::T;
     if (m <= 0) return FAME_OK;
-    const int n1 = c->plan.n[0], n2 = c->plan.n[1];
+    const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
+    const double nm = (double)c->n * m;
     const KParams<R> P = make_params<R>(c);
     const ZCfg z = z_config<R>(c, m);
     fame_status s = set_smem<R>(c, (const void*)k_zin<R>, z.smem);
     if (s != FAME_OK) return s;
     dim3 grid((n1 + z.TP - 1) / z.TP, n2, (m + z.vpc - 1) / z.vpc);
-    k_zin<R><<<grid, z.threads, z.smem, st>>>(P, y, x, m, z.TP, z.vpc);
+    {
+        ProfScope ps(K_ZIN, sizeof(R) == 8, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
+        k_zin<R><<<grid, z.threads, z.smem, st>>>(P, y, x, m, z.TP, z.vpc);
+    }
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
     return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
@@ -700,15 +732,17 @@ fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::
 fame_status run_grad(fame_ctx* c, const double2* Y, const double* w, int nev, double* dB,
                      cudaStream_t st) {
     const size_t N = 3 * (size_t)c->n;
-    fame_status s = grow(c, c->work, 2 * N * sizeof(double2));
+    fame_status s = grow(c, c->work, N * sizeof(double2));
     if (s != FAME_OK) return s;
-    double2* x = reinterpret_cast<double2*>(c->work.p) + N;   // lift output after the workspace half
+    double2* x = reinterpret_cast<double2*>(c->work.p);   // lifted band, [3][n]
     FAME_CUDA_TRY(c, cudaMemsetAsync(dB, 0, N * sizeof(double), st));
     for (int j = 0; j < nev; ++j) {
         if (w[j] == 0.0) continue;
-        // lift into the upper half; the lower half serves as nothing here (zin writes x directly)
         if ((s = run_lift<double>(c, Y + (size_t)j * 2 * c->n, x, 1, st)) != FAME_OK) return s;
-        k_grad_accum<<<1216, 256, 0, st>>>(x, w[j], dB, N);
+        {
+            ProfScope ps(K_GRAD, true, st, (double)N * (sizeof(double2) + 2 * sizeof(double)), 4.0 * N);
+            k_grad_accum<<<1216, 256, 0, st>>>(x, w[j], dB, N);
+        }
         count_launch();
         FAME_CUDA_TRY(c, cudaGetLastError());
     }

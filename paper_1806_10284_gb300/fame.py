@@ -39,6 +39,8 @@ _SIGS = {
     "fame_grad_eps": (C.c_int, [C.c_void_p, C.c_int, _D3, C.c_double, C.c_void_p, C.c_void_p]),
     "fame_eigs_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
                                     C.c_int, _D3, C.POINTER(C.c_int), C.c_void_p]),
+    "fame_profile": (C.c_int, [C.c_int]),
+    "fame_profile_read": (C.c_int, [C.c_void_p, C.c_int]),
     "fame_last_error": (C.c_char_p, [C.c_void_p]),
     "fame_destroy": (None, [C.c_void_p]),
     "fame_launch_count": (C.c_ulonglong, []),
@@ -60,11 +62,30 @@ class PlanInfo(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("iters_mixed", C.c_int), ("iters_fp64", C.c_int), ("applies_c64", C.c_longlong),
-                ("applies_c128", C.c_longlong), ("max_residual", C.c_double)]
+                ("applies_c128", C.c_longlong), ("max_residual", C.c_double),
+                ("rr_host_ms", C.c_double)]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("total_ms", C.c_double),
+                ("bytes", C.c_double), ("flops", C.c_double)]
 
 
 _lib = None
 _lock = threading.Lock()
+
+
+def profile(enable: bool):
+    """Start (clearing old records) or stop per-kernel event timing."""
+    _check(load().fame_profile(1 if enable else 0), None)
+
+
+def profile_read():
+    """{kernel kind: dict(launches, total_ms, bytes, flops)} since profile(True)."""
+    arr = (KernelStat * 64)()
+    k = load().fame_profile_read(C.cast(arr, C.c_void_p), 64)
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms,
+                                       bytes=arr[i].bytes, flops=arr[i].flops) for i in range(k)}
 
 
 def load(path: str = LIB_PATH):
@@ -249,7 +270,7 @@ class Context:
         _check(load().fame_get_stats(self._h, C.byref(s)), self._h)
         return dict(iters_mixed=s.iters_mixed, iters_fp64=s.iters_fp64,
                     applies_c64=s.applies_c64, applies_c128=s.applies_c128,
-                    max_residual=s.max_residual)
+                    max_residual=s.max_residual, rr_host_ms=s.rr_host_ms)
 
     def grad(self, nev, dobj_dlambda, rel_cluster=1e-8, stream=None):
         """dB (float64 CUDA tensor [3][n]) for the last eigs call."""
