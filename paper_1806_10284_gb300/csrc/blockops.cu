@@ -21,11 +21,12 @@ template <> struct Acc<double2> { using T = double; };
 
 template <typename C>
 __device__ __forceinline__ const C* col_ptr(const BlockList<C>& L, int i, size_t ld) {
-    if (i < L.cols[0]) return L.ptr[0] + (size_t)i * ld;
-    i -= L.cols[0];
-    if (i < L.cols[1]) return L.ptr[1] + (size_t)i * ld;
-    i -= L.cols[1];
-    return L.ptr[2] + (size_t)i * ld;
+#pragma unroll
+    for (int b = 0; b < BlockList<C>::kMax - 1; ++b) {
+        if (i < L.cols[b]) return L.ptr[b] + (size_t)i * ld;
+        i -= L.cols[b];
+    }
+    return L.ptr[BlockList<C>::kMax - 1] + (size_t)i * ld;
 }
 
 // partial[blk][j][i] = sum over this block's rows of conj(U_i) V_j  (column-major ku x kv).
@@ -134,17 +135,23 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(BlockList<CU> U, BlockLis
 }
 
 // G = sum over blocks of partial (fixed order, deterministic)
+// One warp per entry: lanes take blocks lane, lane+32, ...; fixed shuffle tree.
 __global__ void k_gram_reduce(const double2* __restrict__ partial, int nblk, int kk,
                               double2* __restrict__ G) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
     if (e >= kk) return;
     double sr = 0.0, si = 0.0;
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = lane; b < nblk; b += 32) {
         const double2 v = partial[(size_t)b * kk + e];
         sr += v.x;
         si += v.y;
     }
-    G[e] = make_double2(sr, si);
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_down_sync(0xffffffffu, sr, o);
+        si += __shfl_down_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) G[e] = make_double2(sr, si);
 }
 
 // out1_j = sum_{i<k} S_i M[i][j];  out2_j = sum_{i>=i0} S_i M[i][j]   (j < m)
@@ -162,15 +169,16 @@ __global__ void k_combine(BlockList<C> S, size_t ld, const double2* __restrict__
     __syncthreads();
     for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < ld;
          row += (size_t)gridDim.x * blockDim.x) {
-        for (int j0 = 0; j0 < m; j0 += 8) {
-            const int jn = min(8, m - j0);
-            C a1[8], a2[8];
+        constexpr int JC = sizeof(R) == 4 ? 16 : 8;   // output columns per pass over S
+        for (int j0 = 0; j0 < m; j0 += JC) {
+            const int jn = min(JC, m - j0);
+            C a1[JC], a2[JC];
 #pragma unroll
-            for (int b = 0; b < 8; ++b) { a1[b] = mk((R)0, (R)0); a2[b] = a1[b]; }
+            for (int b = 0; b < JC; ++b) { a1[b] = mk((R)0, (R)0); a2[b] = a1[b]; }
             for (int i = 0; i < k; ++i) {
                 const C s = col_ptr(S, i, ld)[row];
 #pragma unroll
-                for (int b = 0; b < 8; ++b) {
+                for (int b = 0; b < JC; ++b) {
                     if (b < jn) {
                         const C p = cmul(s, sm[(size_t)(j0 + b) * k + i]);
                         a1[b] = a1[b] + p;
@@ -179,7 +187,7 @@ __global__ void k_combine(BlockList<C> S, size_t ld, const double2* __restrict__
                 }
             }
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
+            for (int b = 0; b < JC; ++b) {
                 if (b < jn) {
                     if (out1) out1[(size_t)(j0 + b) * ld + row] = mk((Ro)a1[b].x, (Ro)a1[b].y);
                     if (out2) out2[(size_t)(j0 + b) * ld + row] = mk((Ro)a2[b].x, (Ro)a2[b].y);
@@ -223,7 +231,8 @@ __global__ void k_resid(const C* __restrict__ X, const C* __restrict__ AX,
 // W_j = tinv .* R_j rounded to complex64; part[j][blk] = partial ||R_j||^2.
 __global__ void k_resid_mixed(const double2* __restrict__ X, const double2* __restrict__ AX,
                               const double* __restrict__ theta, const float* __restrict__ tinv,
-                              size_t n, float2* __restrict__ W, double* __restrict__ part) {
+                              size_t n, float2* __restrict__ W, float2* __restrict__ R32,
+                              double* __restrict__ part) {
     __shared__ double red[32];
     const int j = blockIdx.y;
     const size_t ld = 2 * n;
@@ -236,6 +245,7 @@ __global__ void k_resid_mixed(const double2* __restrict__ X, const double2* __re
         s += rx * rx + ry * ry;
         const float t = tinv[row < n ? row : row - n];
         W[(size_t)j * ld + row] = make_float2(t * (float)rx, t * (float)ry);
+        if (R32) R32[(size_t)j * ld + row] = make_float2((float)rx, (float)ry);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -266,26 +276,27 @@ __global__ void k_combine_mixed(const double2* __restrict__ X, int m, BlockList<
     __syncthreads();
     for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < ld;
          row += (size_t)gridDim.x * blockDim.x) {
-        for (int j0 = 0; j0 < m; j0 += 8) {
-            const int jn = min(8, m - j0);
-            double2 a[8];
-            float2 d[8];
+        constexpr int JC = 8;    // output columns per pass (register budget of the FP64 part)
+        for (int j0 = 0; j0 < m; j0 += JC) {
+            const int jn = min(JC, m - j0);
+            double2 a[JC];
+            float2 d[JC];
 #pragma unroll
-            for (int b = 0; b < 8; ++b) { a[b] = make_double2(0.0, 0.0); d[b] = make_float2(0.f, 0.f); }
+            for (int b = 0; b < JC; ++b) { a[b] = make_double2(0.0, 0.0); d[b] = make_float2(0.f, 0.f); }
             for (int i = 0; i < m; ++i) {
                 const double2 x = X[(size_t)i * ld + row];
 #pragma unroll
-                for (int b = 0; b < 8; ++b)
+                for (int b = 0; b < JC; ++b)
                     if (b < jn) a[b] = a[b] + cmul(x, sd[(size_t)(j0 + b) * m + i]);
             }
             for (int i = 0; i < nq; ++i) {
                 const float2 q = col_ptr(Q, i, ld)[row];
 #pragma unroll
-                for (int b = 0; b < 8; ++b)
+                for (int b = 0; b < JC; ++b)
                     if (b < jn) d[b] = d[b] + cmul(q, sf[(size_t)(j0 + b) * nq + i]);
             }
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
+            for (int b = 0; b < JC; ++b) {
                 if (b < jn) {
                     const size_t o = (size_t)(j0 + b) * ld + row;
                     const double2 v = make_double2(a[b].x + (double)d[b].x, a[b].y + (double)d[b].y);
@@ -313,19 +324,20 @@ __global__ void k_orth(const CX* __restrict__ X, int m, BlockList<CQ> Q, size_t 
     __syncthreads();
     for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < ld;
          row += (size_t)gridDim.x * blockDim.x) {
-        for (int j0 = 0; j0 < nq; j0 += 8) {
-            const int jn = min(8, nq - j0);
-            C a[8];
+        constexpr int JC = sizeof(R) == 4 ? 16 : 8;   // output columns per pass over X
+        for (int j0 = 0; j0 < nq; j0 += JC) {
+            const int jn = min(JC, nq - j0);
+            C a[JC];
 #pragma unroll
-            for (int b = 0; b < 8; ++b) a[b] = mk((R)0, (R)0);
+            for (int b = 0; b < JC; ++b) a[b] = mk((R)0, (R)0);
             for (int i = 0; i < m; ++i) {
                 const C x = X[(size_t)i * ld + row];
 #pragma unroll
-                for (int b = 0; b < 8; ++b)
+                for (int b = 0; b < JC; ++b)
                     if (b < jn) a[b] = a[b] + cmul(x, sc[(size_t)(j0 + b) * m + i]);
             }
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
+            for (int b = 0; b < JC; ++b) {
                 if (b < jn) {
                     CQ* q = const_cast<CQ*>(col_ptr(Q, j0 + b, ld)) + row;
                     const CQ v = *q;
@@ -409,7 +421,7 @@ fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, si
     const int kk = ku * kv;
     {
         ProfScope ps(K_GRAM_RED, dbl, st, (double)nblk * kk * sizeof(double2), 2.0 * nblk * kk);
-        k_gram_reduce<<<(kk + 255) / 256, 256, 0, st>>>(part, nblk, kk, G);
+        k_gram_reduce<<<(kk + 7) / 8, 256, 0, st>>>(part, nblk, kk, G);
     }
     count_launch(2);
     FAME_CUDA_TRY(c, cudaGetLastError());
@@ -451,12 +463,12 @@ fame_status residual(fame_ctx* c, const C* X, const C* AX, const double* theta_d
 }
 
 fame_status residual_mixed(fame_ctx* c, const double2* X, const double2* AX, const double* theta_dev,
-                           int m, float2* W, double* part, int nblk, cudaStream_t st) {
+                           int m, float2* W, float2* R32, double* part, int nblk, cudaStream_t st) {
     dim3 grid(nblk, m);
     {
         const double ld = 2.0 * c->n;
-        ProfScope ps(K_RESID, true, st, m * ld * (2 * sizeof(double2) + sizeof(float2)), 8.0 * m * ld);
-        k_resid_mixed<<<grid, 256, 0, st>>>(X, AX, theta_dev, c->tf.tinv, (size_t)c->n, W, part);
+        ProfScope ps(K_RESID, true, st, m * ld * (2 * sizeof(double2) + (R32 ? 2 : 1) * sizeof(float2)), 8.0 * m * ld);
+        k_resid_mixed<<<grid, 256, 0, st>>>(X, AX, theta_dev, c->tf.tinv, (size_t)c->n, W, R32, part);
     }
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());

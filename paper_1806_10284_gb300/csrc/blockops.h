@@ -5,8 +5,9 @@
 // Up to three column blocks of vectors (each column = 2n complex, leading dim ld).
 template <typename C>
 struct BlockList {
-    const C* ptr[3];
-    int cols[3];
+    static constexpr int kMax = 6;
+    const C* ptr[kMax];
+    int cols[kMax];
     int total;
 };
 
@@ -14,10 +15,25 @@ template <typename C>
 inline BlockList<C> blocks(const C* a, int na, const C* b = nullptr, int nb = 0,
                            const C* c = nullptr, int nc = 0) {
     BlockList<C> L;
+    for (int i = 0; i < BlockList<C>::kMax; ++i) { L.ptr[i] = nullptr; L.cols[i] = 0; }
     L.ptr[0] = a; L.cols[0] = na;
     L.ptr[1] = b; L.cols[1] = nb;
     L.ptr[2] = c; L.cols[2] = nc;
     L.total = na + nb + nc;
+    return L;
+}
+
+// concatenation of two block lists (at most kMax blocks in total)
+template <typename C>
+inline BlockList<C> concat(const BlockList<C>& a, const BlockList<C>& b) {
+    BlockList<C> L = a;
+    int k = 0;
+    while (k < BlockList<C>::kMax && L.cols[k] > 0) ++k;
+    for (int i = 0; i < BlockList<C>::kMax && b.cols[i] > 0 && k < BlockList<C>::kMax; ++i, ++k) {
+        L.ptr[k] = b.ptr[i];
+        L.cols[k] = b.cols[i];
+    }
+    L.total = a.total + b.total;
     return L;
 }
 
@@ -39,9 +55,10 @@ template <typename C>
 fame_status residual(fame_ctx* c, const C* X, const C* AX, const double* theta_dev,
                      const typename RealOf<C>::T* tinv, int m, C* W, double* part, int nblk,
                      cudaStream_t st);
-// refinement: R = AX - X theta from complex128 X, AX (FP64), W = tinv .* R as complex64
+// refinement: R = AX - X theta from complex128 X, AX (FP64), W = tinv .* R as complex64,
+// R32 = R as complex64 (may be null)
 fame_status residual_mixed(fame_ctx* c, const double2* X, const double2* AX, const double* theta_dev,
-                           int m, float2* W, double* part, int nblk, cudaStream_t st);
+                           int m, float2* W, float2* R32, double* part, int nblk, cudaStream_t st);
 // refinement update: Xn = X M[:m] (FP64) + Q M[m:] (FP32), X32n = complex64 copy of Xn,
 // Pn = Q M[m:] (may be null)
 fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<float2>& Q, size_t ld,

@@ -149,15 +149,14 @@ int host_rr(fame_ctx* c, const Small& sm, int k, int m, int implicit_xx, const s
     return got;
 }
 
-// Refinement Rayleigh-Ritz.  The basis is [X W P] with X the complex128 Ritz
-// block of the previous step (X^H X = I, X^H A X = Theta) and Q = [W P] (nq
-// complex64 columns).  Device G holds, in order: Q^H Q (nq x nq), Q^H AQ
-// (nq x nq), and [X AX]^H Q (2m x nq, FP64 products).  The coupling blocks
-// use A X (complex128) rather than A Q.
+// Refinement Rayleigh-Ritz.  The basis is [X Q], X the complex128 Ritz block of
+// the previous step (X^H X = I, X^H A X = Theta) and Q = [W P] (nq complex64
+// columns orthogonalised against X, so X^H Q = 0 and Q^H A X = Q^H R).  Device G
+// holds the nq x (2 nq + m) matrix Q^H [Q | AQ | R], column-major.
 int host_rr_refine(fame_ctx* c, const Small& sm, int m, int nq, const std::vector<double>& theta_prev,
                    double drop, std::vector<double>& theta, std::vector<double2>& Cm, cudaStream_t st,
                    fame_status* err) {
-    const size_t cnt = (size_t)2 * nq * nq + (size_t)2 * m * nq;
+    const size_t cnt = (size_t)nq * (2 * nq + m);
     std::vector<double2> G(cnt);
     cudaError_t e = cudaMemcpyAsync(G.data(), sm.G, cnt * sizeof(double2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -167,9 +166,7 @@ int host_rr_refine(fame_ctx* c, const Small& sm, int m, int nq, const std::vecto
     }
     const auto t0 = std::chrono::steady_clock::now();
     const int k = m + nq;
-    const double2* QQ = G.data();
-    const double2* QAQ = QQ + (size_t)nq * nq;
-    const double2* XQ = QAQ + (size_t)nq * nq;    // (2m) x nq, column-major
+    auto g = [&](int row, int col) { return G[(size_t)col * nq + row]; };
     std::vector<double> GB(2 * (size_t)k * k, 0.0), GA(2 * (size_t)k * k, 0.0);
     auto set = [&](std::vector<double>& M, int i, int j, double re, double im) {
         M[2 * ((size_t)j * k + i)] = re;
@@ -181,13 +178,11 @@ int host_rr_refine(fame_ctx* c, const Small& sm, int m, int nq, const std::vecto
     }
     for (int q = 0; q < nq; ++q) {
         for (int i = 0; i < m; ++i) {
-            const double2 xb = XQ[(size_t)q * 2 * m + i];       // X_i^H Q_q
-            const double2 xa = XQ[(size_t)q * 2 * m + m + i];   // (A X_i)^H Q_q
-            set(GB, m + q, i, xb.x, -xb.y);
-            set(GA, m + q, i, xa.x, -xa.y);
+            const double2 r = g(q, 2 * nq + i);          // Q_q^H R_i = Q_q^H A X_i
+            set(GA, m + q, i, r.x, r.y);
         }
         for (int p = 0; p < nq; ++p) {
-            const double2 b = QQ[(size_t)q * nq + p], a = QAQ[(size_t)q * nq + p];
+            const double2 b = g(p, q), a = g(p, nq + q);
             set(GB, m + p, m + q, b.x, b.y);
             set(GA, m + p, m + q, a.x, a.y);
         }
@@ -262,8 +257,8 @@ fame_status lob_explicit(fame_ctx* c, C* const S[2], C* const AS[2], const Small
         const int k = m + nw + np;
         const BlockList<C> U = blocks<C>(X, m, Wb, nw, Pb, np);
         const BlockList<C> V = blocks<C>(AX, m, AWb, nw, APb, np);
-        if ((s = gram<C, C>(c, U, U, ld, sm.G, st)) != FAME_OK) return s;
-        if ((s = gram<C, C>(c, U, V, ld, sm.G + (size_t)k * k, st)) != FAME_OK) return s;
+        // [GB | GA] = U^H [U | V] in one pass over U
+        if ((s = gram<C, C>(c, U, concat(U, V), ld, sm.G, st)) != FAME_OK) return s;
         std::vector<double> th;
         const int got = host_rr(c, sm, k, m, 0, theta, drop, th, Cm, st, &s);
         if (got < 0) return s;
@@ -337,8 +332,7 @@ fame_status rr64(fame_ctx* c, double2* a, double2* aa, double2* b, double2* ab, 
     fame_status s;
     if (do_apply && (s = apply_block<double2>(c, a, aa, m, st)) != FAME_OK) return s;
     const BlockList<double2> U = blocks<double2>(a, m), V = blocks<double2>(aa, m);
-    if ((s = gram<double2, double2>(c, U, U, ld, sm.G, st)) != FAME_OK) return s;
-    if ((s = gram<double2, double2>(c, U, V, ld, sm.G + (size_t)m * m, st)) != FAME_OK) return s;
+    if ((s = gram<double2, double2>(c, U, concat(U, V), ld, sm.G, st)) != FAME_OK) return s;
     std::vector<double2> Cm;
     std::vector<double> th;
     const int got = host_rr(c, sm, m, m, 0, theta, 1e-14, th, Cm, st, &s);
@@ -357,8 +351,8 @@ fame_status rr64(fame_ctx* c, double2* a, double2* aa, double2* b, double2* ab, 
 // refined complex128 X is in X64[0] with AX in AX64[0].
 // ---------------------------------------------------------------------------
 fame_status lob_refine(fame_ctx* c, float2* const S[2], float2* const AS[2], double2* const X64[2],
-                       double2* const AX64[2], const Small& sm, int m, int nev, double tol, int max_iter,
-                       cudaStream_t st, PhaseOut& out) {
+                       double2* const AX64[2], float2* R32, const Small& sm, int m, int nev, double tol,
+                       int max_iter, cudaStream_t st, PhaseOut& out) {
     const size_t ld = 2 * (size_t)c->n;
     fame_status s;
     std::vector<double> theta(m, 0.0), res;
@@ -375,7 +369,7 @@ fame_status lob_refine(fame_ctx* c, float2* const S[2], float2* const AS[2], dou
         // residuals of the tracked pair; W for every column
         float2* X32 = S[cur];
         float2* AX32 = AS[cur];
-        if ((s = residual_mixed(c, X64[cur], AX64[cur], sm.theta, m, X32 + (size_t)m * ld, sm.part, kResidBlocks, st)) != FAME_OK) return s;
+        if ((s = residual_mixed(c, X64[cur], AX64[cur], sm.theta, m, X32 + (size_t)m * ld, R32, sm.part, kResidBlocks, st)) != FAME_OK) return s;
         if ((s = read_norms(c, sm, m, theta, res, st)) != FAME_OK) return s;
         double worst = 0.0;
         for (int j = 0; j < nev; ++j) worst = std::max(worst, res[j]);
@@ -405,7 +399,7 @@ fame_status lob_refine(fame_ctx* c, float2* const S[2], float2* const AS[2], dou
             if (worst <= tol) { out.converged = true; break; }
             if ((s = convert<double2, float2>(c, X64[cur], X32, (size_t)m * ld, st)) != FAME_OK) return s;
             if ((s = convert<double2, float2>(c, AX64[cur], AX32, (size_t)m * ld, st)) != FAME_OK) return s;
-            if ((s = residual_mixed(c, X64[cur], AX64[cur], sm.theta, m, X32 + (size_t)m * ld, sm.part, kResidBlocks, st)) != FAME_OK) return s;
+            if ((s = residual_mixed(c, X64[cur], AX64[cur], sm.theta, m, X32 + (size_t)m * ld, R32, sm.part, kResidBlocks, st)) != FAME_OK) return s;
             np = 0;
         }
         out.theta = theta;
@@ -420,21 +414,19 @@ fame_status lob_refine(fame_ctx* c, float2* const S[2], float2* const AS[2], dou
         const int nq = nw + np;
         const BlockList<float2> Q = blocks<float2>(Wb, nw, Pb, np);
         const BlockList<float2> AQ = blocks<float2>(AWb, nw, APb, np);
-        // Orthogonalise the complex64 directions against X in FP64 (c = X^H Q,
-        // Q <- Q - X c, AP <- AP - AX c_P) so that no direction carries a large
-        // component along X whose complex64 rounding the Rayleigh-Ritz step would
-        // amplify; then AW for the orthogonalised W.
-        const BlockList<double2> Xl = blocks<double2>(X64[cur], m);
-        if ((s = gram<double2, float2>(c, Xl, Q, ld, sm.G, st)) != FAME_OK) return s;
-        if ((s = orth_against<double2, float2>(c, X64[cur], m, Q, ld, sm.G, st)) != FAME_OK) return s;
-        if (np > 0 && (s = orth_against<double2, float2>(c, AX64[cur], m, blocks<float2>(APb, np), ld, sm.G + (size_t)m * nw, st)) != FAME_OK) return s;
+        // Orthogonalise the complex64 directions against X (c = X^H Q, Q <- Q - X c,
+        // AP <- AP - AX c_P) so that no direction carries a large component along X
+        // whose complex64 rounding the Rayleigh-Ritz step would amplify; then AW for
+        // the orthogonalised W.  With Q orthogonal to X, the coupling Q^H A X equals
+        // Q^H R (R = AX - X Theta, small), so every Gram block is an FP32-product
+        // Gram: Q^H [Q | AQ | R].
+        const BlockList<float2> Xl = blocks<float2>(X32, m);
+        if ((s = gram<float2, float2>(c, Xl, Q, ld, sm.G, st)) != FAME_OK) return s;
+        if ((s = orth_against<float2, float2>(c, X32, m, Q, ld, sm.G, st)) != FAME_OK) return s;
+        if (np > 0 && (s = orth_against<float2, float2>(c, AX32, m, blocks<float2>(APb, np), ld, sm.G + (size_t)m * nw, st)) != FAME_OK) return s;
         if ((s = apply_block<float2>(c, Wb, AWb, nw, st)) != FAME_OK) return s;
-        // W/P blocks, FP32 products: [W P]^H [W P | AW AP]
-        if ((s = gram<float2, float2>(c, Q, Q, ld, sm.G, st)) != FAME_OK) return s;
-        if ((s = gram<float2, float2>(c, Q, AQ, ld, sm.G + (size_t)nq * nq, st)) != FAME_OK) return s;
-        // X rows, FP64 products on the complex128 X and AX: [X AX]^H [W P]
-        const BlockList<double2> XA = blocks<double2>(X64[cur], m, AX64[cur], m);
-        if ((s = gram<double2, float2>(c, XA, Q, ld, sm.G + (size_t)2 * nq * nq, st)) != FAME_OK) return s;
+        const BlockList<float2> V = concat(concat(Q, AQ), blocks<float2>(R32, m));
+        if ((s = gram<float2, float2>(c, Q, V, ld, sm.G, st)) != FAME_OK) return s;
         std::vector<double> th;
         const int got = host_rr_refine(c, sm, m, nq, theta, 1e-6, th, Cm, st, &s);
         if (got < 0) return s;
@@ -467,7 +459,8 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
     const int k = 3 * m;
     size_t bytes = small_bytes(m) + 256;
     if (mixed)
-        bytes += 4 * (((size_t)k * ld * sizeof(float2) + 255)) + 4 * (((size_t)m * ld * sizeof(double2) + 255));
+        bytes += 4 * (((size_t)k * ld * sizeof(float2) + 255)) + 4 * (((size_t)m * ld * sizeof(double2) + 255)) +
+                 (((size_t)m * ld * sizeof(float2) + 255));
     else
         bytes += 4 * (((size_t)k * ld * sizeof(double2) + 255));
     if ((s = grow(c, c->solver, bytes)) != FAME_OK) return s;
@@ -485,13 +478,14 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
         double2* AX64[2];
         for (int i = 0; i < 2; ++i) { S[i] = cv.take<float2>((size_t)k * ld); AS[i] = cv.take<float2>((size_t)k * ld); }
         for (int i = 0; i < 2; ++i) { X64[i] = cv.take<double2>((size_t)m * ld); AX64[i] = cv.take<double2>((size_t)m * ld); }
+        float2* R32 = cv.take<float2>((size_t)m * ld);
         if ((s = random_block<float2>(c, S[0], m, seed, c->tf.tinv, st)) != FAME_OK) return s;
         if (warm && (s = convert<double2, float2>(c, reinterpret_cast<const double2*>(c->Y), S[0], (size_t)nwarm * ld, st)) != FAME_OK) return s;
         const double tol32 = std::max(tol, 2e-5);
         if ((s = lob_explicit<float2>(c, S, AS, sm, m, nev, tol32, max_iter, true, 1e-6, st, ph1)) != FAME_OK) return s;
         c->stats.iters_mixed = ph1.iters;
         const int left = std::max(2, max_iter - ph1.iters);
-        if ((s = lob_refine(c, S, AS, X64, AX64, sm, m, nev, tol, left, st, ph2)) != FAME_OK) return s;
+        if ((s = lob_refine(c, S, AS, X64, AX64, R32, sm, m, nev, tol, left, st, ph2)) != FAME_OK) return s;
         c->stats.iters_fp64 = ph2.iters;
         Xfinal = X64[0];
         const int left2 = max_iter - ph1.iters - ph2.iters;
