@@ -184,6 +184,16 @@ fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::
 fame_status run_grad(fame_ctx* c, const double2* Y, const double* w, int nev, double* dB,
                      cudaStream_t st);
 fame_status run_precond_table(fame_ctx* c, cudaStream_t st);
+
+// fixed-length passes (apply3.cu), complex64
+bool z3_supported(int L);
+bool xy3_supported(int n1, int n2);
+template <typename R>
+fame_status run_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
+                   typename cpx<R>::T* out, int m, bool zin, cudaStream_t st);
+template <typename R>
+fame_status run_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int m, int mode,
+                    R lift_scale, cudaStream_t st);
 fame_status run_basis_mask(fame_ctx* c);
 
 // solver (solver.cu)

@@ -16,114 +16,15 @@
 // a y pass, an x pass and a y pass.  All DFTs are shared-memory Stockham
 // passes (radix 2, 3, 4, 5, 8) with precomputed twiddle tables; twist phases
 // and Lambda_l are evaluated in the kernels from exact fractions.
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "fame_internal.h"
+#include "fft2.cuh"
+#include "phases.cuh"
 
 namespace {
-
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-// Reference vector switch: the paper's e = (1,1,1) unless 3 Lq - |Ls|^2 < G_TOL * 3 Lq.
-constexpr double kGTol = 1.0 / 16.0;
-
-// ---------------------------------------------------------------------------
-// phases
-// ---------------------------------------------------------------------------
-// idx * f mod 1, in [-1/2, 1/2]
-__device__ __forceinline__ float frac_mul(int idx, Frac32 f) {
-    float t = (float)idx * f.hi;  // exact: idx < 1024, hi a multiple of 2^-13
-    t -= rintf(t);
-    t = fmaf((float)idx, f.lo, t);
-    return t - rintf(t);
-}
-__device__ __forceinline__ double frac_mul(int idx, double f) {
-    double t = (double)idx * f;
-    return t - rint(t);
-}
-// e^{+2 pi i phi}, |phi| <= 1/2
-__device__ __forceinline__ float2 cis(float phi) {
-    float s, c;
-    __sincosf((float)kTwoPi * phi, &s, &c);
-    return make_float2(c, s);
-}
-__device__ __forceinline__ double2 cis(double phi) {
-    double s, c;
-    sincospi(2.0 * phi, &s, &c);
-    return make_double2(c, s);
-}
-// Lambda = (e^{2 pi i (idx + L f)/L} - 1) * inv_delta, evaluated as
-// 2 i sin(pi x) e^{i pi x} * inv_delta with x = (idx + L f)/L reduced to [-1/2, 1/2)
-// in exact arithmetic first, so small |x| keeps full relative precision.
-__device__ __forceinline__ float2 lambda_of(int idx, int L, Frac32 f, float inv_delta) {
-    const float Lf = (float)L;
-    float u = Lf * f.hi;                 // exact
-    float t = (float)idx + u;            // exact (< 2048, 13 fractional bits)
-    if (t >= 0.5f * Lf) t -= Lf;
-    if (t >= 0.5f * Lf) t -= Lf;
-    t = fmaf(Lf, f.lo, t);
-    float x = t / Lf;
-    if (x >= 0.5f) x -= 1.0f;
-    if (x < -0.5f) x += 1.0f;
-    float s, c;
-    sincospif(x, &s, &c);
-    return make_float2(-2.0f * s * s * inv_delta, 2.0f * s * c * inv_delta);
-}
-__device__ __forceinline__ double2 lambda_of(int idx, int L, double f, double inv_delta) {
-    double t = (double)idx + (double)L * f;
-    double x = t / (double)L;
-    x -= rint(x);
-    double s, c;
-    sincospi(x, &s, &c);
-    return make_double2(-2.0 * s * s * inv_delta, 2.0 * s * c * inv_delta);
-}
-
-__device__ __forceinline__ bool alt_bit(const uint32_t* mask, size_t f) {
-    return (mask[f >> 5] >> (f & 31)) & 1u;
-}
-
-template <typename R>
-struct Basis {
-    typename cpx<R>::T p1[3], p2[3];
-    R sig;
-};
-
-// Pi_1, Pi_2 of eqs. (range_basis1), (range_basis2) with unit columns, and
-// Sigma_r = Lq^{1/2} (eq. SVD); reference vector e = (1,1,1), or (1,-1,0)
-// where Lambda is close to parallel to (1,1,1) (alt, read from the FP64 mask).
-template <typename R>
-__device__ __forceinline__ Basis<R> make_basis(typename cpx<R>::T L0, typename cpx<R>::T L1,
-                                                typename cpx<R>::T L2, bool alt) {
-    using C = typename cpx<R>::T;
-    Basis<R> b;
-    const R Lq = L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y + L2.x * L2.x + L2.y * L2.y;
-    if (!(Lq > (R)0)) {
-        b.sig = (R)0;
-        for (int l = 0; l < 3; ++l) { b.p1[l] = mk((R)0, (R)0); b.p2[l] = mk((R)0, (R)0); }
-        return b;
-    }
-    const R e0 = (R)1, e1 = alt ? (R)-1 : (R)1, e2 = alt ? (R)0 : (R)1;
-    const C ed = mk(e0 * L0.x + e1 * L1.x + e2 * L2.x, e0 * L0.y + e1 * L1.y + e2 * L2.y);
-    const R een = alt ? (R)2 : (R)3;
-    const R g = een * Lq - (ed.x * ed.x + ed.y * ed.y);
-    const R r1 = (R)1 / sqrt(Lq * g);
-    const R r2 = (R)1 / sqrt(g);
-    // Pi_1 = (Lq e - Lambda conj(e.Lambda)) / sqrt(Lq g)
-    const C edc = conjc(ed);
-    const C m0 = cmul(L0, edc), m1 = cmul(L1, edc), m2 = cmul(L2, edc);
-    b.p1[0] = mk((Lq * e0 - m0.x) * r1, -m0.y * r1);
-    b.p1[1] = mk((Lq * e1 - m1.x) * r1, -m1.y * r1);
-    b.p1[2] = mk((Lq * e2 - m2.x) * r1, -m2.y * r1);
-    // Pi_2 = conj(e x Lambda) / sqrt(g)
-    const C x0 = e1 * L2 - e2 * L1;
-    const C x1 = e2 * L0 - e0 * L2;
-    const C x2 = e0 * L1 - e1 * L0;
-    b.p2[0] = mk(x0.x * r2, -x0.y * r2);
-    b.p2[1] = mk(x1.x * r2, -x1.y * r2);
-    b.p2[2] = mk(x2.x * r2, -x2.y * r2);
-    b.sig = sqrt(Lq);
-    return b;
-}
-
 // ---------------------------------------------------------------------------
 // Stockham radix butterflies
 // ---------------------------------------------------------------------------
@@ -265,11 +166,6 @@ __device__ C* fft_axis(C* a, C* b, const Pencils& P, const AxisPlan& A, const C*
         b = t;
     }
     return a;
-}
-
-template <typename C>
-__device__ __forceinline__ void load_table(C* dst, const C* src, int L) {
-    for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -579,6 +475,190 @@ __global__ void k_precond(KParams<R> P, R* __restrict__ tinv, R mean_invB) {
 }
 
 // ---------------------------------------------------------------------------
+// Two-level kernels for the lengths fft2::supported accepts: the same passes
+// as k_zin / k_xy / k_zout, with register-resident radix-R1 and radix-R2 DFTs,
+// one twiddled shared-memory exchange per transform, pencils mapped to
+// consecutive lanes, and planes stored with an odd row stride.
+// ---------------------------------------------------------------------------
+// q / d for 0 <= q < 2^20, d <= 1024, via a float reciprocal (exact in that range)
+__device__ __forceinline__ int fdiv(int q, float inv_d) { return __float2int_rz(((float)q + 0.5f) * inv_d); }
+
+template <typename R>
+__global__ void __launch_bounds__(512) k_zin2(KParams<R> P, const typename cpx<R>::T* __restrict__ y,
+                                              typename cpx<R>::T* __restrict__ W, int m, int lgTP,
+                                              int vpc) {
+    using C = typename cpx<R>::T;
+    using F = typename FracT<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
+    const int TP = 1 << lgTP, NP = 3 * TP;
+    const size_t n = (size_t)n1 * n2 * n3;
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* L0s = tw + n3;
+    C* L1s = L0s + TP;
+    F* F3s = reinterpret_cast<F*>(L1s + TP);
+    C* X = L1s + 2 * TP;                 // F3s occupies TP entries of C size
+    C* Y = X + (size_t)n3 * NP;
+    const int q = blockIdx.y, p0 = blockIdx.x * TP;
+    load_table(tw, P.tw[2], n3);
+    for (int pp = threadIdx.x; pp < TP; pp += blockDim.x) {
+        const int p = min(p0 + pp, n1 - 1);
+        L0s[pp] = lambda_of(p, n1, P.f1, P.inv_dx);
+        L1s[pp] = lambda_of(q, n2, P.f2[p], P.inv_dy);
+        F3s[pp] = P.f3[(size_t)q * n1 + p];
+    }
+    __syncthreads();
+    const int tile = n3 * TP;
+    const int v1 = min(m, (int)(blockIdx.z + 1) * vpc);
+    for (int v = blockIdx.z * vpc; v < v1; ++v) {
+        const C* yv = y + (size_t)v * 2 * n;
+        for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+            const int r = e >> lgTP, pp = e & (TP - 1), p = p0 + pp;
+            C o0 = mk((R)0, (R)0), o1 = o0, o2 = o0;
+            if (p < n1) {
+                const size_t f = ((size_t)r * n2 + q) * n1 + p;
+                const C y1 = yv[f], y2 = yv[n + f];
+                const C L2 = lambda_of(r, n3, F3s[pp], P.inv_dz);
+                const Basis<R> b = make_basis<R>(L0s[pp], L1s[pp], L2, alt_bit(P.alt, f));
+                const C s1 = b.sig * y1, s2 = b.sig * y2;
+                o0 = cmul(b.p1[0], s1) + cmul(b.p2[0], s2);
+                o1 = cmul(b.p1[1], s1) + cmul(b.p2[1], s2);
+                o2 = cmul(b.p1[2], s1) + cmul(b.p2[2], s2);
+            }
+            X[r * NP + pp] = o0;
+            X[r * NP + TP + pp] = o1;
+            X[r * NP + 2 * TP + pp] = o2;
+        }
+        __syncthreads();
+        C* Wv = W + (size_t)v * 3 * n;
+        fft2::pencils_any<true>(
+            n3, NP, tw, Y, [&](int pc, int e) { return X[e * NP + pc]; },
+            [&](int pc, int c, C val) {
+                const int l = pc >> lgTP, pp = pc & (TP - 1), p = p0 + pp;
+                if (p < n1)
+                    Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p] = cmul(val, cis(frac_mul(c, F3s[pp])));
+            });
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) k_zout2(KParams<R> P, const typename cpx<R>::T* __restrict__ W,
+                                               typename cpx<R>::T* __restrict__ out, int m, int lgTP,
+                                               int vpc) {
+    using C = typename cpx<R>::T;
+    using F = typename FracT<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
+    const int TP = 1 << lgTP, NP = 3 * TP;
+    const size_t n = (size_t)n1 * n2 * n3;
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* L0s = tw + n3;
+    C* L1s = L0s + TP;
+    F* F3s = reinterpret_cast<F*>(L1s + TP);
+    C* X = L1s + 2 * TP;
+    C* Y = X + (size_t)n3 * NP;
+    const int q = blockIdx.y, p0 = blockIdx.x * TP;
+    load_table(tw, P.tw[2], n3);
+    for (int pp = threadIdx.x; pp < TP; pp += blockDim.x) {
+        const int p = min(p0 + pp, n1 - 1);
+        L0s[pp] = lambda_of(p, n1, P.f1, P.inv_dx);
+        L1s[pp] = lambda_of(q, n2, P.f2[p], P.inv_dy);
+        F3s[pp] = P.f3[(size_t)q * n1 + p];
+    }
+    __syncthreads();
+    const int tile = n3 * TP;
+    const int v1 = min(m, (int)(blockIdx.z + 1) * vpc);
+    for (int v = blockIdx.z * vpc; v < v1; ++v) {
+        const C* Wv = W + (size_t)v * 3 * n;
+        fft2::pencils_any<false>(
+            n3, NP, tw, Y,
+            [&](int pc, int c) {
+                const int l = pc >> lgTP, pp = pc & (TP - 1), p = p0 + pp;
+                if (p >= n1) return mk((R)0, (R)0);
+                const C x = Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p];
+                return cmulc(cis(frac_mul(c, F3s[pp])), x);
+            },
+            [&](int pc, int r, C val) { X[r * NP + pc] = val; });
+        C* ov = out + (size_t)v * 2 * n;
+        for (int e = threadIdx.x; e < tile; e += blockDim.x) {
+            const int r = e >> lgTP, pp = e & (TP - 1), p = p0 + pp;
+            if (p < n1) {
+                const size_t f = ((size_t)r * n2 + q) * n1 + p;
+                const C L2 = lambda_of(r, n3, F3s[pp], P.inv_dz);
+                const Basis<R> b = make_basis<R>(L0s[pp], L1s[pp], L2, alt_bit(P.alt, f));
+                const C w0 = X[r * NP + pp], w1 = X[r * NP + TP + pp], w2 = X[r * NP + 2 * TP + pp];
+                const C z1 = cmulc(b.p1[0], w0) + cmulc(b.p1[1], w1) + cmulc(b.p1[2], w2);
+                const C z2 = cmulc(b.p2[0], w0) + cmulc(b.p2[1], w1) + cmulc(b.p2[2], w2);
+                ov[f] = b.sig * z1;
+                ov[n + f] = b.sig * z2;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One z-plane per block; plane kept with row stride n1 + 1.
+template <typename R>
+__global__ void __launch_bounds__(512) k_xy2(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode,
+                                             R lift_scale) {
+    using C = typename cpx<R>::T;
+    using F = typename FracT<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
+    const int np = n1 * n2, S = n1 + 1;
+    C* twx = reinterpret_cast<C*>(smem_raw);
+    C* twy = twx + n1;
+    F* F2s = reinterpret_cast<F*>(twy + n2);
+    C* X = twy + n2 + n1;                // F2s occupies n1 entries of C size
+    C* Y = X + (size_t)n2 * S;
+    const int plane = blockIdx.x;
+    const int c = plane % n3;
+    const int l = (plane / n3) % 3;
+    C* g = W + (size_t)plane * np;
+    const float inv_n1 = 1.0f / (float)n1;
+    load_table(twx, P.tw[0], n1);
+    load_table(twy, P.tw[1], n2);
+    for (int p = threadIdx.x; p < n1; p += blockDim.x) F2s[p] = P.f2[p];
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+        const int b = fdiv(e, inv_n1), a = e - b * n1;
+        X[b * S + a] = g[e];
+    }
+    __syncthreads();
+    // inverse y-DFT over columns, then D_a2
+    fft2::pencils_any<true>(
+        n2, n1, twy, Y, [&](int p, int b) { return X[b * S + p]; },
+        [&](int p, int b, C v) { X[b * S + p] = cmul(v, cis(frac_mul(b, F2s[p]))); });
+    // inverse x-DFT over rows
+    fft2::pencils_any<true>(
+        n1, n2, twx, Y, [&](int b, int a) { return X[b * S + a]; },
+        [&](int b, int a, C v) { X[b * S + a] = v; });
+    const R* ib = P.invB + (size_t)l * n3 * np + (size_t)c * np;
+    if (mode == 0) {
+        for (int e = threadIdx.x; e < np; e += blockDim.x) {
+            const int b = fdiv(e, inv_n1), a = e - b * n1;
+            X[b * S + a] = (ib[e] * P.scale) * X[b * S + a];
+        }
+        __syncthreads();
+        fft2::pencils_any<false>(
+            n1, n2, twx, Y, [&](int b, int a) { return X[b * S + a]; },
+            [&](int b, int a, C v) { X[b * S + a] = v; });
+        fft2::pencils_any<false>(
+            n2, n1, twy, Y,
+            [&](int p, int b) { return cmulc(cis(frac_mul(b, F2s[p])), X[b * S + p]); },
+            [&](int p, int b, C v) { X[b * S + p] = v; });
+        for (int e = threadIdx.x; e < np; e += blockDim.x) {
+            const int b = fdiv(e, inv_n1), a = e - b * n1;
+            g[e] = X[b * S + a];
+        }
+    } else {
+        for (int e = threadIdx.x; e < np; e += blockDim.x) {
+            const int b = fdiv(e, inv_n1), a = e - b * n1;
+            g[e] = (ib[e] * lift_scale) * cmul(X[b * S + a], cis(frac_mul(a, P.f1)));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launch configuration
 // ---------------------------------------------------------------------------
 constexpr size_t kSmemCap = 200 * 1024;
@@ -614,6 +694,37 @@ ZCfg z_config(const fame_ctx* c, int m) {
     return z;
 }
 
+// Two-level Z-pass configuration (TP a power of two).
+struct Z2Cfg { int lgTP, vpc, threads; size_t smem; bool ok; };
+
+template <typename R>
+Z2Cfg z2_config(const fame_ctx* c, int m) {
+    using C = typename cpx<R>::T;
+    const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
+    Z2Cfg z;
+    z.ok = fft2::supported(n3);
+    int TP = 16;
+    while (TP > 1 && (size_t)(n3 + 3 * TP + 6 * (size_t)TP * n3) * sizeof(C) > kSmemCap) TP /= 2;
+    while (TP > 1 && TP > n1) TP /= 2;
+    z.lgTP = 0;
+    while ((1 << z.lgTP) < TP) ++z.lgTP;
+    z.smem = (size_t)(n3 + 3 * TP + 6 * (size_t)TP * n3) * sizeof(C);
+    const fft2::Split sp = fft2::split_of(n3);
+    const int work = 3 * TP * std::max(sp.R1, sp.R2);
+    z.threads = std::min(512, std::max(128, ((work + 31) / 32) * 32));
+    const long long tiles = (long long)((n1 + TP - 1) / TP) * n2;
+    z.vpc = 1;
+    while (z.vpc < m && tiles * ((m + z.vpc * 2 - 1) / (z.vpc * 2)) >= 152 * 6) z.vpc *= 2;
+    if (z.smem > kSmemCap) z.ok = false;
+    return z;
+}
+
+template <typename R>
+size_t xy2_smem(int n1, int n2) {
+    using C = typename cpx<R>::T;
+    return (size_t)(2 * n1 + n2 + (size_t)n2 * (n1 + 1) + (size_t)n1 * n2) * sizeof(C);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -631,6 +742,23 @@ static fame_status xy_stage(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T
     const double nm = (double)c->n * m;
     const size_t plane_smem = (size_t)(n1 + n2 + 2 * n1 * n2) * sizeof(C);
     fame_status s;
+    if constexpr (std::is_same<R, float>::value) {
+        if (xy3_supported(n1, n2)) return run_xy3<R>(c, P, W, m, mode, lift_scale, st);
+    }
+    const size_t smem2 = xy2_smem<R>(n1, n2);
+    if (fft2::supported(n1) && fft2::supported(n2) && smem2 <= kSmemCap) {
+        if ((s = set_smem<R>(c, (const void*)k_xy2<R>, smem2)) != FAME_OK) return s;
+        const fft2::Split sx = fft2::split_of(n1), sy = fft2::split_of(n2);
+        const int work = std::max(n1 * std::max(sy.R1, sy.R2), n2 * std::max(sx.R1, sx.R2));
+        const int th = std::min(512, std::max(128, ((work + 31) / 32) * 32));
+        const double bytes = 2.0 * 3 * nm * sizeof(C) + 3.0 * c->n * sizeof(R);
+        const double flops = 3 * nm * 5.0 * (mode == 0 ? 2.0 : 1.0) * (lg2(n1) + lg2(n2));
+        ProfScope ps(K_XY, dbl, st, bytes, flops);
+        k_xy2<R><<<(unsigned)(3LL * m * n3), th, smem2, st>>>(P, W, mode, lift_scale);
+        count_launch();
+        FAME_CUDA_TRY(c, cudaGetLastError());
+        return FAME_OK;
+    }
     if (plane_smem <= kSmemCap) {
         if ((s = set_smem<R>(c, (const void*)k_xy<R>, plane_smem)) != FAME_OK) return s;
         const int th = (n1 * n2 >= 2048) ? 512 : 256;
@@ -687,6 +815,34 @@ fame_status run_apply(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>:
     if (s != FAME_OK) return s;
     C* W = reinterpret_cast<C*>(c->work.p);
     const KParams<R> P = make_params<R>(c);
+    if constexpr (std::is_same<R, float>::value) {
+        if (z3_supported(n3)) {
+            if ((s = run_z3<R>(c, P, y, W, m, true, st)) != FAME_OK) return s;
+            if ((s = xy_stage<R>(c, P, W, m, 0, (R)0, st)) != FAME_OK) return s;
+            return run_z3<R>(c, P, W, Ay, m, false, st);
+        }
+    }
+    const Z2Cfg z2 = z2_config<R>(c, m);
+    if (z2.ok) {
+        if ((s = set_smem<R>(c, (const void*)k_zin2<R>, z2.smem)) != FAME_OK) return s;
+        if ((s = set_smem<R>(c, (const void*)k_zout2<R>, z2.smem)) != FAME_OK) return s;
+        const int TP = 1 << z2.lgTP;
+        dim3 grid((n1 + TP - 1) / TP, n2, (m + z2.vpc - 1) / z2.vpc);
+        {
+            ProfScope ps(K_ZIN, dbl, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
+            k_zin2<R><<<grid, z2.threads, z2.smem, st>>>(P, y, W, m, z2.lgTP, z2.vpc);
+        }
+        count_launch();
+        FAME_CUDA_TRY(c, cudaGetLastError());
+        if ((s = xy_stage<R>(c, P, W, m, 0, (R)0, st)) != FAME_OK) return s;
+        {
+            ProfScope ps(K_ZOUT, dbl, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
+            k_zout2<R><<<grid, z2.threads, z2.smem, st>>>(P, W, Ay, m, z2.lgTP, z2.vpc);
+        }
+        count_launch();
+        FAME_CUDA_TRY(c, cudaGetLastError());
+        return FAME_OK;
+    }
     const ZCfg z = z_config<R>(c, m);
     if ((s = set_smem<R>(c, (const void*)k_zin<R>, z.smem)) != FAME_OK) return s;
     if ((s = set_smem<R>(c, (const void*)k_zout<R>, z.smem)) != FAME_OK) return s;
@@ -716,8 +872,28 @@ fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::
     const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
     const double nm = (double)c->n * m;
     const KParams<R> P = make_params<R>(c);
+    fame_status s;
+    if constexpr (std::is_same<R, float>::value) {
+        if (z3_supported(n3)) {
+            if ((s = run_z3<R>(c, P, y, x, m, true, st)) != FAME_OK) return s;
+            return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
+        }
+    }
+    const Z2Cfg z2 = z2_config<R>(c, m);
+    if (z2.ok) {
+        if ((s = set_smem<R>(c, (const void*)k_zin2<R>, z2.smem)) != FAME_OK) return s;
+        const int TP = 1 << z2.lgTP;
+        dim3 grid((n1 + TP - 1) / TP, n2, (m + z2.vpc - 1) / z2.vpc);
+        {
+            ProfScope ps(K_ZIN, sizeof(R) == 8, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
+            k_zin2<R><<<grid, z2.threads, z2.smem, st>>>(P, y, x, m, z2.lgTP, z2.vpc);
+        }
+        count_launch();
+        FAME_CUDA_TRY(c, cudaGetLastError());
+        return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
+    }
     const ZCfg z = z_config<R>(c, m);
-    fame_status s = set_smem<R>(c, (const void*)k_zin<R>, z.smem);
+    s = set_smem<R>(c, (const void*)k_zin<R>, z.smem);
     if (s != FAME_OK) return s;
     dim3 grid((n1 + z.TP - 1) / z.TP, n2, (m + z.vpc - 1) / z.vpc);
     {

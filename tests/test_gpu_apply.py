@@ -29,6 +29,11 @@ CASES = [
     ("mono80", (20, 24, 16)),
     ("tri192", (18, 15, 8)),     # triclinic, ragged x tiles
     ("fcc64", (2, 2, 2)),        # smallest grid
+    # lengths with fixed-length complex64 passes
+    ("tri192", (32, 32, 48)),    # XY 32x32, Z 48
+    ("mono80", (48, 48, 32)),    # XY 48x48, Z 32
+    ("hex96", (20, 32, 16)),     # Z 16 with a ragged x tile, generic XY
+    ("bcc96", (80, 96, 16)),     # XY 80x96
 ]
 
 
@@ -112,9 +117,21 @@ def test_apply_block_sizes(m):
         assert _rel(got[j], ref) < TOL64
 
 
+@pytest.mark.parametrize("m", [1, 7, 40])
+def test_apply_block_sizes_complex64(m):
+    """Several vectors per block in the fixed-length Z passes."""
+    lat, ctx, invB, rng = _setup("fcc64", (16, 16, 32), seed=m)
+    y = rng.standard_normal((m, 2 * lat.n)) + 1j * rng.standard_normal((m, 2 * lat.n))
+    got = ctx.apply(torch.as_tensor(y, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    for j in sorted({0, m // 2, m - 1}):
+        ref = apply_Ar(lat, y[j].reshape((2,) + lat.shape), invB).ravel()
+        assert _rel(got[j], ref) < TOL32
+
+
+@pytest.mark.parametrize("n", [(12, 10, 8), (16, 16, 16)])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
-def test_lift_matches_oracle(prec):
-    lat, ctx, invB, rng = _setup("tri192", (12, 10, 8), seed=3)
+def test_lift_matches_oracle(prec, n):
+    lat, ctx, invB, rng = _setup("tri192", n, seed=3)
     y = rng.standard_normal((2, 2 * lat.n)) + 1j * rng.standard_normal((2, 2 * lat.n))
     dt = torch.complex128 if prec == "c128" else torch.complex64
     got = ctx.lift(torch.as_tensor(y, dtype=dt, device="cuda")).cpu().numpy()
