@@ -160,6 +160,27 @@ FAME_API fame_status fame_set_eps_device(fame_ctx* ctx, const double* B, void* s
 FAME_API fame_status fame_apply_Ar(fame_ctx* ctx, const void* y, void* Ay, int m, int dtype, void* stream);
 
 /*
+ * fame_apply_Ar_static -- the same A_r y as fame_apply_Ar, computed in a
+ * workspace the library reserves statically in device memory, so that the
+ * call allocates no device memory (the paper has no counterpart: it is an
+ * interface for callers that may not allocate -- code running under a
+ * memory budget fixed by a framework's caching allocator, or latency-bound
+ * loops where a cudaMalloc, which can synchronise the device, is not
+ * acceptable).
+ *   The workspace holds 3 m n complex entries of type dtype and is limited to
+ *   FAME_STATIC_WORKSPACE_BYTES (32 MiB: e.g. m <= 5 complex64 vectors at
+ *   64^3); larger requests fail with FAME_E_ARG and allocate nothing.
+ *   The first call on a device looks up the workspace address (set-up, once
+ *   per device, with that device current); make it before any stream capture.
+ *   The workspace is shared by all contexts of the process on a device:
+ *   calls that overlap in time race on it.  Its contents need no
+ *   initialisation.  Arguments, layout and other errors as fame_apply_Ar.
+ */
+#define FAME_STATIC_WORKSPACE_BYTES (32u << 20)
+FAME_API fame_status fame_apply_Ar_static(fame_ctx* ctx, const void* y, void* Ay, int m, int dtype,
+                                          void* stream);
+
+/*
  * fame_lift -- x = B^{-1} Q_r Sigma_r y, the GEP eigenvector for an A_r
  * eigenvector y (below Theorem invariant_space).
  *   y : device [m][2][n]; x : device [m][3][n] (E1, E2, E3 on the Yee grid);

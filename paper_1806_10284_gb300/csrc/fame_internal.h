@@ -178,6 +178,10 @@ fame_status eps_from_device(fame_ctx* c, const double* B, cudaStream_t st, doubl
 template <typename R>
 fame_status run_apply(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* Ay, int m,
                       cudaStream_t st);
+// the same apply with a caller-provided workspace of 3 m n complex entries
+template <typename R>
+fame_status run_apply_into(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* Ay, int m,
+                           typename cpx<R>::T* W, cudaStream_t st);
 template <typename R>
 fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* x, int m,
                      cudaStream_t st);

@@ -807,13 +807,21 @@ fame_status run_apply(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>:
                       cudaStream_t st) {
     using C = typename cpx<R>::T;
     if (m <= 0) return FAME_OK;
-    const bool dbl = sizeof(R) == 8;
-    const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
-    const double nm = (double)c->n * m;
     const size_t need = (size_t)m * 3 * (size_t)c->n * sizeof(C);
     fame_status s = grow(c, c->work, need);
     if (s != FAME_OK) return s;
-    C* W = reinterpret_cast<C*>(c->work.p);
+    return run_apply_into<R>(c, y, Ay, m, reinterpret_cast<C*>(c->work.p), st);
+}
+
+template <typename R>
+fame_status run_apply_into(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* Ay, int m,
+                           typename cpx<R>::T* W, cudaStream_t st) {
+    using C = typename cpx<R>::T;
+    if (m <= 0) return FAME_OK;
+    const bool dbl = sizeof(R) == 8;
+    const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
+    const double nm = (double)c->n * m;
+    fame_status s;
     const KParams<R> P = make_params<R>(c);
     if constexpr (std::is_same<R, float>::value) {
         if (z3_supported(n3)) {
@@ -951,5 +959,8 @@ fame_status run_precond_table(fame_ctx* c, cudaStream_t st) {
 
 template fame_status run_apply<float>(fame_ctx*, const float2*, float2*, int, cudaStream_t);
 template fame_status run_apply<double>(fame_ctx*, const double2*, double2*, int, cudaStream_t);
+template fame_status run_apply_into<float>(fame_ctx*, const float2*, float2*, int, float2*, cudaStream_t);
+template fame_status run_apply_into<double>(fame_ctx*, const double2*, double2*, int, double2*,
+                                            cudaStream_t);
 template fame_status run_lift<float>(fame_ctx*, const float2*, float2*, int, cudaStream_t);
 template fame_status run_lift<double>(fame_ctx*, const double2*, double2*, int, cudaStream_t);

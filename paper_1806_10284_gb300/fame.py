@@ -32,6 +32,7 @@ _SIGS = {
     "fame_set_eps": (C.c_int, [C.c_void_p, _D3, _D3, _D3, C.c_void_p]),
     "fame_set_eps_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "fame_apply_Ar": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "fame_apply_Ar_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "fame_lift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "fame_eigs": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, _D3, C.c_void_p,
                             C.POINTER(C.c_int), C.c_void_p]),
@@ -237,6 +238,17 @@ class Context:
             out = torch.empty_like(y)
         _check(load().fame_apply_Ar(self._h, _ptr(y), _ptr(out), m, _dtype_code(y), _stream(stream)),
                self._h)
+        return out
+
+    def apply_static(self, y, out, stream=None):
+        """A_r y into a caller-provided ``out`` through the entry point that allocates no
+        device memory (workspace limited to FAME_STATIC_WORKSPACE_BYTES)."""
+        y = y.contiguous()
+        m = y.numel() // (2 * self.N)
+        if m * 2 * self.N != y.numel() or out.shape != y.shape or out.dtype != y.dtype:
+            raise ValueError("y must hold m vectors of 2n entries and out must match it")
+        _check(load().fame_apply_Ar_static(self._h, _ptr(y), _ptr(out), m, _dtype_code(y),
+                                           _stream(stream)), self._h)
         return out
 
     def lift(self, y, stream=None):
