@@ -1,19 +1,19 @@
-// Tall-skinny block operations of the block eigensolver: Gram matrices with
-// FP64 accumulation, block linear combinations, residuals with the
+// Tall-skinny block operations of the block eigensolver: Gram matrices (FP64
+// sums across row blocks), block linear combinations, residuals with the
 // preconditioner, and precision conversion.  Vectors are 2n complex, stored
 // vector-major ([m][2n]).
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
 #include "blockops.h"
+#include "df64.cuh"
 
 namespace {
 
-// per-thread register tile of the Gram kernel
-constexpr int TI = 4;
-constexpr int TJ = 4;
-constexpr int TROWS = 32;          // rows staged in shared memory per step
-constexpr int FLUSH_TILES = 4;     // FP32 partial sums flushed to FP64 every 4 x 32 rows
+// Gram kernel: GT x GT complex outputs per thread, GROWS rows per shared-memory stage
+constexpr int GT = 4;
+constexpr int GROWS = 32;
 
 template <typename C> struct Acc;
 template <> struct Acc<float2> { using T = float; };
@@ -29,108 +29,130 @@ __device__ __forceinline__ const C* col_ptr(const BlockList<C>& L, int i, size_t
     return L.ptr[BlockList<C>::kMax - 1] + (size_t)i * ld;
 }
 
+// asynchronous 8- or 16-byte global -> shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async_c(float2* dst, const float2* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_c(double2* dst, const double2* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory row strides of the Gram stages: room for the padded tile columns,
+// odd (in elements) so that the row-wise staging stores are conflict-free.
+__host__ __device__ inline int gram_stride(int k) {
+    const int s = ((k + GT - 1) / GT) * GT;
+    return s | 1;
+}
+
 // partial[blk][j][i] = sum over this block's rows of conj(U_i) V_j  (column-major ku x kv).
-// Each thread owns a TI x TJ tile of (i, j) pairs; blockIdx.y picks a group of
-// at most kGramThreads tiles.  Complex64 inputs: FP32 products summed in FP32
-// over FLUSH_TILES x TROWS rows, then added into FP64 accumulators kept in
-// shared memory.  Complex128 inputs: FP64 throughout.
+// Thread (ti, tj) owns outputs i = ti + TIN a, j = tj + TJN b (a, b < GT), so a warp
+// reads consecutive V columns and few U columns of each staged row.  Rows arrive in
+// stages of GROWS by cp.async, double-buffered.  Complex64 inputs: FP32 products
+// summed in FP32 over the block's rows (about a thousand), the blocks then summed
+// in FP64 by k_gram_reduce.  Complex128 inputs: FP64 throughout.
 constexpr int kGramThreads = 512;
 
 template <typename CU, typename CV>
 __global__ void __launch_bounds__(kGramThreads) k_gram(BlockList<CU> U, BlockList<CV> V, size_t ld,
                                                       size_t rows_per_blk,
                                                       double2* __restrict__ partial) {
-    // products in FP64 when either side is complex128
     using R = typename std::conditional<(sizeof(CU) == 16 || sizeof(CV) == 16), double, float>::type;
-    using C = typename cpx<R>::T;
     using RU = typename Acc<CU>::T;
     using RV = typename Acc<CV>::T;
-    constexpr bool kSplit = sizeof(R) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ku = U.total, kv = V.total;
-    CU* su = reinterpret_cast<CU*>(smem_raw);                        // [TROWS][ku]
-    CV* sv = reinterpret_cast<CV*>(su + TROWS * ku);                 // [TROWS][kv]
-    double2* acc64 = reinterpret_cast<double2*>(sv + TROWS * kv);    // [TI*TJ][blockDim]
-    const int tiles_i = (ku + TI - 1) / TI, tiles_j = (kv + TJ - 1) / TJ;
+    const int SU = gram_stride(ku), SV = gram_stride(kv);
+    const int TIN = (ku + GT - 1) / GT, TJN = (kv + GT - 1) / GT;
+    CU* su = reinterpret_cast<CU*>(smem_raw);                  // [2][GROWS][SU]
+    CV* sv = reinterpret_cast<CV*>(su + 2 * GROWS * SU);       // [2][GROWS][SV]
+    const CU** pu = reinterpret_cast<const CU**>(sv + 2 * GROWS * SV);   // column bases [ku]
+    const CV** pv = reinterpret_cast<const CV**>(pu + ku);               // [kv]
+    for (int i = threadIdx.x; i < ku; i += blockDim.x) pu[i] = col_ptr(U, i, ld);
+    for (int j = threadIdx.x; j < kv; j += blockDim.x) pv[j] = col_ptr(V, j, ld);
     const int tile = blockIdx.y * blockDim.x + threadIdx.x;
-    const int ti = tile / tiles_j, tj = tile % tiles_j;
-    const bool active = ti < tiles_i;
+    const int ti = tile / TJN, tj = tile - ti * TJN;
+    const bool active = ti < TIN;
     const size_t r0 = blockIdx.x * rows_per_blk;
     const size_t r1 = min(ld, r0 + rows_per_blk);
-    R accr[TI][TJ], acci[TI][TJ];
-#pragma unroll
-    for (int a = 0; a < TI; ++a)
-#pragma unroll
-        for (int b = 0; b < TJ; ++b) accr[a][b] = acci[a][b] = 0;
-    if (kSplit)
-        for (int q = 0; q < TI * TJ; ++q) acc64[q * blockDim.x + threadIdx.x] = make_double2(0.0, 0.0);
-    int tiles_done = 0;
-    for (size_t rb = r0; rb < r1; rb += TROWS) {
-        const int nr = (int)min((size_t)TROWS, r1 - rb);
-        for (int e = threadIdx.x; e < TROWS * ku; e += blockDim.x) {
-            const int i = e / TROWS, t = e % TROWS;
-            su[t * ku + i] = (t < nr) ? col_ptr(U, i, ld)[rb + t] : mk((RU)0, (RU)0);
+    // padding columns (never loaded) stay zero
+    for (int e = threadIdx.x; e < 2 * GROWS; e += blockDim.x) {
+        for (int i = ku; i < SU; ++i) su[e * SU + i] = mk((RU)0, (RU)0);
+        for (int j = kv; j < SV; ++j) sv[e * SV + j] = mk((RV)0, (RV)0);
+    }
+    __syncthreads();
+    const auto stage = [su, sv, pu, pv, ku, kv, SU, SV, r1](size_t rb, int buf) {
+        const int nr = (int)min((size_t)GROWS, r1 - rb);
+        CU* du = su + buf * GROWS * SU;
+        CV* dv = sv + buf * GROWS * SV;
+        for (int e = threadIdx.x; e < GROWS * ku; e += blockDim.x) {
+            const int i = e / GROWS, t = e - i * GROWS;
+            cp_async_c(&du[t * SU + i], pu[i] + rb + (t < nr ? t : 0), t < nr);
         }
-        for (int e = threadIdx.x; e < TROWS * kv; e += blockDim.x) {
-            const int j = e / TROWS, t = e % TROWS;
-            sv[t * kv + j] = (t < nr) ? col_ptr(V, j, ld)[rb + t] : mk((RV)0, (RV)0);
+        for (int e = threadIdx.x; e < GROWS * kv; e += blockDim.x) {
+            const int j = e / GROWS, t = e - j * GROWS;
+            cp_async_c(&dv[t * SV + j], pv[j] + rb + (t < nr ? t : 0), t < nr);
+        }
+        cp_async_commit();
+    };
+    R accr[GT][GT], acci[GT][GT];
+#pragma unroll
+    for (int a = 0; a < GT; ++a)
+#pragma unroll
+        for (int b = 0; b < GT; ++b) accr[a][b] = acci[a][b] = 0;
+    const int nst = (int)((r1 - r0 + GROWS - 1) / GROWS);
+    if (nst > 0) stage(r0, 0);
+    for (int s = 0; s < nst; ++s) {
+        if (s + 1 < nst) {
+            stage(r0 + (size_t)(s + 1) * GROWS, (s + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
         if (active) {
-#pragma unroll 2
-            for (int t = 0; t < TROWS; ++t) {
-                C u[TI], w[TJ];
+            const CU* bu = su + (s & 1) * GROWS * SU + ti;
+            const CV* bv = sv + (s & 1) * GROWS * SV + tj;
+#pragma unroll 4
+            for (int t = 0; t < GROWS; ++t) {
+                R ur[GT], ui[GT], wr[GT], wi[GT];
 #pragma unroll
-                for (int a = 0; a < TI; ++a) {
-                    const int i = ti * TI + a;
-                    const CU x = (i < ku) ? su[t * ku + i] : mk((RU)0, (RU)0);
-                    u[a] = mk((R)x.x, (R)x.y);
+                for (int a = 0; a < GT; ++a) {
+                    const CU x = bu[t * SU + TIN * a];
+                    ur[a] = (R)x.x;
+                    ui[a] = (R)x.y;
                 }
 #pragma unroll
-                for (int b = 0; b < TJ; ++b) {
-                    const int j = tj * TJ + b;
-                    const CV x = (j < kv) ? sv[t * kv + j] : mk((RV)0, (RV)0);
-                    w[b] = mk((R)x.x, (R)x.y);
+                for (int b = 0; b < GT; ++b) {
+                    const CV x = bv[t * SV + TJN * b];
+                    wr[b] = (R)x.x;
+                    wi[b] = (R)x.y;
                 }
 #pragma unroll
-                for (int a = 0; a < TI; ++a)
+                for (int a = 0; a < GT; ++a)
 #pragma unroll
-                    for (int b = 0; b < TJ; ++b) {
-                        accr[a][b] = fma(u[a].x, w[b].x, fma(u[a].y, w[b].y, accr[a][b]));
-                        acci[a][b] = fma(u[a].x, w[b].y, fma(-u[a].y, w[b].x, acci[a][b]));
+                    for (int b = 0; b < GT; ++b) {
+                        accr[a][b] = fma(ur[a], wr[b], fma(ui[a], wi[b], accr[a][b]));
+                        acci[a][b] = fma(ur[a], wi[b], fma(-ui[a], wr[b], acci[a][b]));
                     }
             }
         }
         __syncthreads();
-        if (kSplit && ++tiles_done == FLUSH_TILES) {
-            tiles_done = 0;
-#pragma unroll
-            for (int a = 0; a < TI; ++a)
-#pragma unroll
-                for (int b = 0; b < TJ; ++b) {
-                    double2& d = acc64[(a * TJ + b) * blockDim.x + threadIdx.x];
-                    d.x += (double)accr[a][b];
-                    d.y += (double)acci[a][b];
-                    accr[a][b] = acci[a][b] = 0;
-                }
-        }
     }
     if (!active) return;
     double2* out = partial + (size_t)blockIdx.x * ku * kv;
 #pragma unroll
-    for (int a = 0; a < TI; ++a)
+    for (int a = 0; a < GT; ++a)
 #pragma unroll
-        for (int b = 0; b < TJ; ++b) {
-            const int i = ti * TI + a, j = tj * TJ + b;
-            if (i < ku && j < kv) {
-                double xr = (double)accr[a][b], xi = (double)acci[a][b];
-                if (kSplit) {
-                    const double2 d = acc64[(a * TJ + b) * blockDim.x + threadIdx.x];
-                    xr += d.x;
-                    xi += d.y;
-                }
-                out[(size_t)j * ku + i] = make_double2(xr, xi);
-            }
+        for (int b = 0; b < GT; ++b) {
+            const int i = ti + TIN * a, j = tj + TJN * b;
+            if (i < ku && j < kv) out[(size_t)j * ku + i] = make_double2((double)accr[a][b], (double)acci[a][b]);
         }
 }
 
@@ -156,41 +178,72 @@ __global__ void k_gram_reduce(const double2* __restrict__ partial, int nblk, int
 
 // out1_j = sum_{i<k} S_i M[i][j];  out2_j = sum_{i>=i0} S_i M[i][j]   (j < m)
 // M column-major k x m double2 in device memory, rounded once into shared memory
-// in the block's precision; accumulation in that precision.
+// ([i][j], outputs padded to a multiple of CJ) in the block's precision;
+// accumulation in that precision.  A thread owns CR rows (r, r + 32) by CJ
+// consecutive outputs; a warp covers 64 consecutive rows of one output group,
+// so its loads of S are coalesced and its coefficient reads are broadcasts.
+constexpr int CR = 2, CJ = 8, kCombineThreads = 256, kCombineSlots = 2;
+
 template <typename C, typename Co>
-__global__ void k_combine(BlockList<C> S, size_t ld, const double2* __restrict__ M, int m, int i0,
-                          Co* __restrict__ out1, Co* __restrict__ out2) {
+__global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, size_t ld, const double2* __restrict__ M,
+                                                             int m, int i0, Co* __restrict__ out1,
+                                                             Co* __restrict__ out2) {
     using R = typename Acc<C>::T;
     using Ro = decltype(Co().x);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int k = S.total;
-    C* sm = reinterpret_cast<C*>(smem_raw);
-    for (int e = threadIdx.x; e < k * m; e += blockDim.x) sm[e] = mk((R)M[e].x, (R)M[e].y);
+    const int k = S.total, ng = (m + CJ - 1) / CJ, MP = ng * CJ;
+    C* sm = reinterpret_cast<C*>(smem_raw);                        // [k][MP]
+    const C** ps = reinterpret_cast<const C**>(sm + (size_t)k * MP); // column bases [k]
+    for (int e = threadIdx.x; e < k * MP; e += blockDim.x) {
+        const int i = e / MP, j = e - i * MP;
+        sm[e] = j < m ? mk((R)M[(size_t)j * k + i].x, (R)M[(size_t)j * k + i].y) : mk((R)0, (R)0);
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) ps[i] = col_ptr(S, i, ld);
     __syncthreads();
-    for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < ld;
-         row += (size_t)gridDim.x * blockDim.x) {
-        constexpr int JC = sizeof(R) == 4 ? 16 : 8;   // output columns per pass over S
-        for (int j0 = 0; j0 < m; j0 += JC) {
-            const int jn = min(JC, m - j0);
-            C a1[JC], a2[JC];
+    constexpr int TPS = kCombineThreads / kCombineSlots;         // threads per output-group slot
+    const int slot = threadIdx.x / TPS, lt = threadIdx.x % TPS;
+    const size_t span = (size_t)TPS * CR;                         // rows per block step
+    for (size_t base = blockIdx.x * span; base < ld; base += (size_t)gridDim.x * span) {
+        const size_t ra = base + (size_t)(lt >> 5) * 64 + (lt & 31), rb = ra + 32;
+        const bool va = ra < ld, vb = rb < ld;
+        for (int g = slot; g < ng; g += kCombineSlots) {
+            C a1[CR][CJ], a2[CR][CJ];
 #pragma unroll
-            for (int b = 0; b < JC; ++b) { a1[b] = mk((R)0, (R)0); a2[b] = a1[b]; }
-            for (int i = 0; i < k; ++i) {
-                const C s = col_ptr(S, i, ld)[row];
+            for (int r = 0; r < CR; ++r)
 #pragma unroll
-                for (int b = 0; b < JC; ++b) {
-                    if (b < jn) {
-                        const C p = cmul(s, sm[(size_t)(j0 + b) * k + i]);
-                        a1[b] = a1[b] + p;
-                        if (i >= i0) a2[b] = a2[b] + p;
-                    }
+                for (int j = 0; j < CJ; ++j) a1[r][j] = a2[r][j] = mk((R)0, (R)0);
+            const C* cf = sm + g * CJ;
+            for (int i = 0; i < i0 && i < k; ++i) {
+                const C xa = va ? ps[i][ra] : mk((R)0, (R)0);
+                const C xb = vb ? ps[i][rb] : mk((R)0, (R)0);
+#pragma unroll
+                for (int j = 0; j < CJ; ++j) {
+                    const C w = cf[(size_t)i * MP + j];
+                    a1[0][j] = a1[0][j] + cmul(xa, w);
+                    a1[1][j] = a1[1][j] + cmul(xb, w);
+                }
+            }
+            for (int i = i0; i < k; ++i) {
+                const C xa = va ? ps[i][ra] : mk((R)0, (R)0);
+                const C xb = vb ? ps[i][rb] : mk((R)0, (R)0);
+#pragma unroll
+                for (int j = 0; j < CJ; ++j) {
+                    const C w = cf[(size_t)i * MP + j];
+                    a2[0][j] = a2[0][j] + cmul(xa, w);
+                    a2[1][j] = a2[1][j] + cmul(xb, w);
                 }
             }
 #pragma unroll
-            for (int b = 0; b < JC; ++b) {
-                if (b < jn) {
-                    if (out1) out1[(size_t)(j0 + b) * ld + row] = mk((Ro)a1[b].x, (Ro)a1[b].y);
-                    if (out2) out2[(size_t)(j0 + b) * ld + row] = mk((Ro)a2[b].x, (Ro)a2[b].y);
+            for (int j = 0; j < CJ; ++j) {
+                const int jj = g * CJ + j;
+                if (jj >= m) break;
+#pragma unroll
+                for (int r = 0; r < CR; ++r) {
+                    const size_t row = r == 0 ? ra : rb;
+                    if (row >= ld) continue;
+                    const C t = a1[r][j] + a2[r][j];
+                    if (out1) out1[(size_t)jj * ld + row] = mk((Ro)t.x, (Ro)t.y);
+                    if (out2) out2[(size_t)jj * ld + row] = mk((Ro)a2[r][j].x, (Ro)a2[r][j].y);
                 }
             }
         }
@@ -257,53 +310,74 @@ __global__ void k_resid_mixed(const double2* __restrict__ X, const double2* __re
     }
 }
 
-// Refinement update of one of (X, AX):
-//   Xn_j  = sum_{i<m} X_i M[i][j] (FP64) + Dn_j,   Dn_j = sum_{i<nq} Q_i M[m+i][j] (FP32),
-//   X32n_j = Xn_j rounded to complex64, and Pn_j = Dn_j (complex64).
-// The FP32 part carries the search-direction correction, whose size shrinks with the residual.
-__global__ void k_combine_mixed(const double2* __restrict__ X, int m, BlockList<float2> Q, size_t ld,
-                                const double2* __restrict__ M, double2* __restrict__ Xn,
-                                float2* __restrict__ X32n, float2* __restrict__ Pn) {
+// Refinement update Xn = X M[:m] + Q M[m:] with X complex128.  The X part is
+// summed in double-float arithmetic (df64.cuh: FP64-accurate, FP32 instructions;
+// the native FP64 rate of this GPU is a small fraction of its FP32 rate), the Q
+// part (a correction orthogonal to X) in FP32.  Outputs: Xn (complex128), its
+// complex64 copy X32n, and Pn = Q M[m:] (complex64, may be null).  M column-major
+// k x m, k = m + nq; its X rows are split into float pairs once per block.
+constexpr int MJ = 8;   // output columns per pass over the inputs
+
+__global__ void __launch_bounds__(256) k_combine_mixed(const double2* __restrict__ X, int m, BlockList<float2> Q,
+                                                       size_t ld, const double2* __restrict__ M,
+                                                       double2* __restrict__ Xn, float2* __restrict__ X32n,
+                                                       float2* __restrict__ Pn) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nq = Q.total, k = m + nq;
-    double2* sd = reinterpret_cast<double2*>(smem_raw);          // M rows 0..m-1, FP64
-    float2* sf = reinterpret_cast<float2*>(sd + (size_t)m * m);  // M rows m..k-1, FP32
-    for (int e = threadIdx.x; e < k * m; e += blockDim.x) {
-        const int j = e / k, i = e % k;
-        if (i < m) sd[(size_t)j * m + i] = M[e];
-        else sf[(size_t)j * nq + (i - m)] = make_float2((float)M[e].x, (float)M[e].y);
+    const int nq = Q.total, k = m + nq, ng = (m + MJ - 1) / MJ, MP = ng * MJ;
+    float4* cx = reinterpret_cast<float4*>(smem_raw);               // [m][MP]: (re h, re l, im h, im l)
+    float2* cq = reinterpret_cast<float2*>(cx + (size_t)m * MP);     // [nq][MP]
+    const float2** qp = reinterpret_cast<const float2**>(cq + (size_t)nq * MP);
+    for (int e = threadIdx.x; e < k * MP; e += blockDim.x) {
+        const int i = e / MP, j = e - i * MP;
+        const double2 v = j < m ? M[(size_t)j * k + i] : make_double2(0.0, 0.0);
+        if (i < m) {
+            const float rh = (float)v.x, ih = (float)v.y;
+            cx[e] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+        } else {
+            cq[e - (size_t)m * MP] = make_float2((float)v.x, (float)v.y);
+        }
     }
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) qp[i] = col_ptr(Q, i, ld);
     __syncthreads();
     for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < ld;
          row += (size_t)gridDim.x * blockDim.x) {
-        constexpr int JC = 8;    // output columns per pass (register budget of the FP64 part)
-        for (int j0 = 0; j0 < m; j0 += JC) {
-            const int jn = min(JC, m - j0);
-            double2 a[JC];
-            float2 d[JC];
+        for (int g = 0; g < ng; ++g) {
+            float Sr[MJ], Er[MJ], Si[MJ], Ei[MJ];
+            float2 d[MJ];
 #pragma unroll
-            for (int b = 0; b < JC; ++b) { a[b] = make_double2(0.0, 0.0); d[b] = make_float2(0.f, 0.f); }
+            for (int j = 0; j < MJ; ++j) {
+                Sr[j] = Er[j] = Si[j] = Ei[j] = 0.0f;
+                d[j] = make_float2(0.0f, 0.0f);
+            }
             for (int i = 0; i < m; ++i) {
                 const double2 x = X[(size_t)i * ld + row];
+                const df64::Split xr = df64::split(x.x), xi = df64::split(x.y);
+                const float4* c = cx + (size_t)i * MP + g * MJ;
 #pragma unroll
-                for (int b = 0; b < JC; ++b)
-                    if (b < jn) a[b] = a[b] + cmul(x, sd[(size_t)(j0 + b) * m + i]);
+                for (int j = 0; j < MJ; ++j) {
+                    const float4 w = c[j];
+                    // (xr + i xi)(wr + i wi): re = xr wr - xi wi, im = xr wi + xi wr
+                    df64::mac(Sr[j], Er[j], xr.h, xr.l, w.x, w.y);
+                    df64::mac(Sr[j], Er[j], -xi.h, -xi.l, w.z, w.w);
+                    df64::mac(Si[j], Ei[j], xr.h, xr.l, w.z, w.w);
+                    df64::mac(Si[j], Ei[j], xi.h, xi.l, w.x, w.y);
+                }
             }
             for (int i = 0; i < nq; ++i) {
-                const float2 q = col_ptr(Q, i, ld)[row];
+                const float2 q = qp[i][row];
+                const float2* c = cq + (size_t)i * MP + g * MJ;
 #pragma unroll
-                for (int b = 0; b < JC; ++b)
-                    if (b < jn) d[b] = d[b] + cmul(q, sf[(size_t)(j0 + b) * nq + i]);
+                for (int j = 0; j < MJ; ++j) d[j] = d[j] + cmul(q, c[j]);
             }
 #pragma unroll
-            for (int b = 0; b < JC; ++b) {
-                if (b < jn) {
-                    const size_t o = (size_t)(j0 + b) * ld + row;
-                    const double2 v = make_double2(a[b].x + (double)d[b].x, a[b].y + (double)d[b].y);
-                    Xn[o] = v;
-                    X32n[o] = make_float2((float)v.x, (float)v.y);
-                    if (Pn) Pn[o] = d[b];
-                }
+            for (int j = 0; j < MJ; ++j) {
+                const int jj = g * MJ + j;
+                if (jj >= m) break;
+                const size_t o = (size_t)jj * ld + row;
+                const float er = Er[j] + d[j].x, ei = Ei[j] + d[j].y;
+                Xn[o] = make_double2(df64::widen(Sr[j]) + df64::widen(er), df64::widen(Si[j]) + df64::widen(ei));
+                X32n[o] = make_float2(Sr[j] + er, Si[j] + ei);
+                if (Pn) Pn[o] = d[j];
             }
         }
     }
@@ -396,16 +470,17 @@ template <typename CU, typename CV>
 fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, size_t ld,
                  double2* G, cudaStream_t st) {
     const int ku = U.total, kv = V.total;
-    const int tiles = ((ku + TI - 1) / TI) * ((kv + TJ - 1) / TJ);
+    const int tiles = ((ku + GT - 1) / GT) * ((kv + GT - 1) / GT);
     const int groups = (tiles + kGramThreads - 1) / kGramThreads;
     int threads = (((tiles + groups - 1) / groups + 31) / 32) * 32;
     if (threads < 64) threads = 64;
     const bool dbl = sizeof(CU) == 16 || sizeof(CV) == 16;
-    const size_t smem = (size_t)TROWS * (ku * sizeof(CU) + kv * sizeof(CV)) +
-                        (dbl ? 0 : (size_t)TI * TJ * threads * sizeof(double2));
-    int nblk = 152 * 4;
+    const size_t smem = (size_t)2 * GROWS * (gram_stride(ku) * sizeof(CU) + gram_stride(kv) * sizeof(CV)) +
+                        (size_t)(ku + kv) * sizeof(void*);
+    // three blocks per SM; each block's rows summed in the block's precision
+    int nblk = 152 * 3;
     size_t rpb = (ld + nblk - 1) / nblk;
-    rpb = ((rpb + TROWS - 1) / TROWS) * TROWS;
+    rpb = ((rpb + GROWS - 1) / GROWS) * GROWS;
     nblk = (int)((ld + rpb - 1) / rpb);
     fame_status s = grow(c, c->partial, (size_t)nblk * ku * kv * sizeof(double2));
     if (s != FAME_OK) return s;
@@ -431,7 +506,8 @@ fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, si
 template <typename C, typename Co>
 fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2* M, int m, int i0,
                     Co* out1, Co* out2, cudaStream_t st) {
-    const size_t smem = (size_t)S.total * m * sizeof(C);
+    const int MP = ((m + CJ - 1) / CJ) * CJ;
+    const size_t smem = (size_t)S.total * MP * sizeof(C) + (size_t)S.total * sizeof(void*);
     if (smem > 48 * 1024)
         FAME_CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_combine<C, Co>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -439,7 +515,9 @@ fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2
         const double outs = (out1 ? m : 0) + (out2 ? m : 0);
         ProfScope ps(K_COMBINE, sizeof(C) == sizeof(double2), st,
                      (double)S.total * ld * sizeof(C) + outs * ld * sizeof(Co), 8.0 * S.total * outs * (double)ld);
-        k_combine<C, Co><<<152 * 8, 256, smem, st>>>(S, ld, M, m, i0, out1, out2);
+        const size_t span = (size_t)(kCombineThreads / kCombineSlots) * CR;
+        const unsigned nblk = (unsigned)std::min<size_t>(152 * 4, (ld + span - 1) / span);
+        k_combine<C, Co><<<nblk, kCombineThreads, smem, st>>>(S, ld, M, m, i0, out1, out2);
     }
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
@@ -478,7 +556,8 @@ fame_status residual_mixed(fame_ctx* c, const double2* X, const double2* AX, con
 fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<float2>& Q, size_t ld,
                           const double2* M, double2* Xn, float2* X32n, float2* Pn, cudaStream_t st) {
     const int nq = Q.total;
-    const size_t smem = (size_t)m * m * sizeof(double2) + (size_t)nq * m * sizeof(float2);
+    const int MP = ((m + MJ - 1) / MJ) * MJ;
+    const size_t smem = (size_t)m * MP * sizeof(float4) + (size_t)nq * MP * sizeof(float2) + (size_t)nq * sizeof(void*);
     if (smem > 48 * 1024)
         FAME_CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_combine_mixed,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -42,7 +42,8 @@ template <> struct RealOf<float2> { using T = float; };
 template <> struct RealOf<double2> { using T = double; };
 
 // G (column-major ku x kv, double2, device) = U^H V; FP64 products when either side is
-// complex128, else FP32 products with FP64 accumulation
+// complex128, else FP32 products summed in FP32 over row blocks of about a thousand
+// rows and in FP64 across the blocks
 template <typename CU, typename CV>
 fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, size_t ld, double2* G,
                  cudaStream_t st);

@@ -178,3 +178,35 @@ def test_autograd_function():
     g_ref = objective_gradient(lat, 1.0 / B, V, lam_ref, c, rel_tol=1e-8).ravel()
     np.testing.assert_allclose(Bt.grad.cpu().numpy(), g_ref, rtol=1e-7,
                                atol=1e-9 * np.abs(g_ref).max())
+
+
+def _fcc64_context():
+    w = W.WORKLOADS["fcc64"]
+    K = W.bloch_vectors("fcc64")[0]
+    ctx = fame.Context(w["vectors"], w["n"], K)
+    lat = make_lattice(w["vectors"], w["n"], K)
+    geom = ctx.geometry()
+    B = W.eps_for("fcc64", geom)
+    ctx.set_eps(*B)
+    return ctx, lat, np.stack([1.0 / b for b in B])
+
+
+@pytest.mark.parametrize("flags,rtol", [(fame.FAME_MIXED, 1e-5), (fame.FAME_FP64, 1e-10)])
+def test_fcc64_full_size_against_oracle_golden(flags, rtol):
+    """The FCC 64^3 workload at full size: the 10 eigenvalues against the oracle's
+    (tests/golden/fcc64_eigs.json, written by make_fcc64_eigs.py from oracle/ alone),
+    and three of the GPU eigenpairs re-checked with the oracle's own FP64 apply."""
+    import json
+    import os
+    from oracle.nfsep import apply_Ar
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fcc64_eigs.json")))
+    ctx, lat, invB = _fcc64_context()
+    lam, Y, it = ctx.eigs(10, tol=1e-8, flags=flags, vectors=True)
+    np.testing.assert_allclose(lam, gold["eigenvalues"], rtol=rtol)
+    assert ctx.stats()["max_residual"] <= 1e-8
+    Yh = Y.cpu().numpy()
+    for j in (0, 1, 9):                       # a degenerate-looking pair and the top band
+        y = Yh[j].reshape((2,) + lat.shape)
+        r = apply_Ar(lat, y, invB).ravel() - lam[j] * Yh[j]
+        assert np.linalg.norm(r) <= 1.05e-8 * lam[j] * np.linalg.norm(Yh[j])
+    ctx.close()
