@@ -4,6 +4,8 @@
 // vector-major ([m][2n]).
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
+#include <unordered_map>
 #include <type_traits>
 
 #include "blockops.h"
@@ -119,8 +121,8 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(BlockList<CU> U, BlockLis
         if (active) {
             const CU* bu = su + (s & 1) * GROWS * SU + ti;
             const CV* bv = sv + (s & 1) * GROWS * SV + tj;
-#pragma unroll 4
-            for (int t = 0; t < GROWS; ++t) {
+#pragma unroll 1
+            for (int t = 0; t < GROWS; ++t) {   // not unrolled: 83 registers, two 288-thread blocks per SM
                 R ur[GT], ui[GT], wr[GT], wi[GT];
 #pragma unroll
                 for (int a = 0; a < GT; ++a) {
@@ -156,13 +158,127 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(BlockList<CU> U, BlockLis
         }
 }
 
+// Hermitian pair of Gram blocks of LOBPCG: partial[blk] = [U^H U | U^H V] over the
+// block's rows (ku x 2ku, column-major), V = A U, for the entries on or below the
+// diagonal of each block only (both are Hermitian; the consumer rebuilds the upper
+// triangles from the lower ones).  Thread: one contiguous GT x GT tile of one
+// block, tiles of the lower triangle enumerated row by row.  Same staging and
+// precision as k_gram.
+__host__ __device__ inline int herm_stride(int ku) {
+    // row stride of the staged rows in elements: 16-byte aligned, 16 mod 128 bytes
+    const int s = ((ku + GT - 1) / GT) * GT;
+    return s + ((2 - s % 16) + 16) % 16;
+}
+
+// four consecutive complex values from 16-byte aligned shared memory, in 16-byte loads
+__device__ __forceinline__ void load4(const float2* p, float2* v) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(const double2* p, double2* v) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = p[a];
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kGramThreads) k_gram_herm(BlockList<C> U, BlockList<C> V, size_t ld,
+                                                           size_t rows_per_blk, double2* __restrict__ partial) {
+    using R = typename Acc<C>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ku = U.total, SP = herm_stride(ku);
+    const int T = (ku + GT - 1) / GT, ntri = T * (T + 1) / 2;
+    C* su = reinterpret_cast<C*>(smem_raw);                    // [2][GROWS][SP]
+    C* sv = su + 2 * GROWS * SP;                               // [2][GROWS][SP]
+    const C** pu = reinterpret_cast<const C**>(sv + 2 * GROWS * SP);
+    const C** pv = pu + ku;
+    for (int i = threadIdx.x; i < ku; i += blockDim.x) {
+        pu[i] = col_ptr(U, i, ld);
+        pv[i] = col_ptr(V, i, ld);
+    }
+    for (int e = threadIdx.x; e < 2 * GROWS; e += blockDim.x)
+        for (int i = ku; i < SP; ++i) su[e * SP + i] = sv[e * SP + i] = mk((R)0, (R)0);
+    const int tile = blockIdx.y * blockDim.x + threadIdx.x;
+    const bool active = tile < 2 * ntri;
+    const int sblk = active ? tile / ntri : 0, tr = active ? tile - sblk * ntri : 0;
+    int ti = (int)((sqrtf(8.0f * tr + 1.0f) - 1.0f) * 0.5f);
+    while (ti * (ti + 1) / 2 > tr) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= tr) ++ti;
+    const int tj = tr - ti * (ti + 1) / 2;
+    const size_t r0 = blockIdx.x * rows_per_blk;
+    const size_t r1 = min(ld, r0 + rows_per_blk);
+    __syncthreads();
+    const auto stage = [su, sv, pu, pv, ku, SP, r1](size_t rb, int buf) {
+        const int nr = (int)min((size_t)GROWS, r1 - rb);
+        C* du = su + buf * GROWS * SP;
+        C* dv = sv + buf * GROWS * SP;
+        for (int e = threadIdx.x; e < GROWS * ku; e += blockDim.x) {
+            const int i = e / GROWS, t = e - i * GROWS;
+            const size_t off = rb + (t < nr ? t : 0);
+            cp_async_c(&du[t * SP + i], pu[i] + off, t < nr);
+            cp_async_c(&dv[t * SP + i], pv[i] + off, t < nr);
+        }
+        cp_async_commit();
+    };
+    R accr[GT][GT], acci[GT][GT];
+#pragma unroll
+    for (int a = 0; a < GT; ++a)
+#pragma unroll
+        for (int b = 0; b < GT; ++b) accr[a][b] = acci[a][b] = 0;
+    const int nst = (int)((r1 - r0 + GROWS - 1) / GROWS);
+    if (nst > 0) stage(r0, 0);
+    for (int st = 0; st < nst; ++st) {
+        if (st + 1 < nst) {
+            stage(r0 + (size_t)(st + 1) * GROWS, (st + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        if (active) {
+            const C* bu = su + (st & 1) * GROWS * SP + ti * GT;
+            const C* bw = (sblk == 0 ? su : sv) + (st & 1) * GROWS * SP + tj * GT;
+#pragma unroll 1
+            for (int t = 0; t < GROWS; ++t) {
+                static_assert(GT == 4, "load4 stages four columns");
+                C u[GT], w[GT];
+                load4(bu + t * SP, u);
+                load4(bw + t * SP, w);
+#pragma unroll
+                for (int a = 0; a < GT; ++a)
+#pragma unroll
+                    for (int b = 0; b < GT; ++b) {
+                        accr[a][b] = fma(u[a].x, w[b].x, fma(u[a].y, w[b].y, accr[a][b]));
+                        acci[a][b] = fma(u[a].x, w[b].y, fma(-u[a].y, w[b].x, acci[a][b]));
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    double2* out = partial + (size_t)blockIdx.x * ku * 2 * ku + (size_t)sblk * ku * ku;
+#pragma unroll
+    for (int a = 0; a < GT; ++a)
+#pragma unroll
+        for (int b = 0; b < GT; ++b) {
+            const int i = ti * GT + a, j = tj * GT + b;
+            if (i < ku && j < ku) out[(size_t)j * ku + i] = make_double2((double)accr[a][b], (double)acci[a][b]);
+        }
+}
+
 // G = sum over blocks of partial (fixed order, deterministic)
 // One warp per entry: lanes take blocks lane, lane+32, ...; fixed shuffle tree.
+// herm_k > 0: the Hermitian pair layout of k_gram_herm (k x 2k); entries above the
+// diagonal of either block were not computed and are set to zero.
 __global__ void k_gram_reduce(const double2* __restrict__ partial, int nblk, int kk,
-                              double2* __restrict__ G) {
+                              double2* __restrict__ G, int herm_k) {
     const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (e >= kk) return;
+    if (herm_k > 0 && (e / herm_k) % herm_k > e % herm_k) {
+        if (lane == 0) G[e] = make_double2(0.0, 0.0);
+        return;
+    }
     double sr = 0.0, si = 0.0;
     for (int b = lane; b < nblk; b += 32) {
         const double2 v = partial[(size_t)b * kk + e];
@@ -213,6 +329,7 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
 #pragma unroll
                 for (int j = 0; j < CJ; ++j) a1[r][j] = a2[r][j] = mk((R)0, (R)0);
             const C* cf = sm + g * CJ;
+#pragma unroll 4
             for (int i = 0; i < i0 && i < k; ++i) {
                 const C xa = va ? ps[i][ra] : mk((R)0, (R)0);
                 const C xb = vb ? ps[i][rb] : mk((R)0, (R)0);
@@ -223,6 +340,7 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
                     a1[1][j] = a1[1][j] + cmul(xb, w);
                 }
             }
+#pragma unroll 4
             for (int i = i0; i < k; ++i) {
                 const C xa = va ? ps[i][ra] : mk((R)0, (R)0);
                 const C xb = vb ? ps[i][rb] : mk((R)0, (R)0);
@@ -384,38 +502,67 @@ __global__ void __launch_bounds__(256) k_combine_mixed(const double2* __restrict
 }
 
 // Q_j <- Q_j - sum_i X_i c[i][j] for the nq columns of Q (in place), c m x nq
-// column-major.  Arithmetic in FP64 when X is complex128, else FP32.
+// column-major.  Arithmetic in FP64 when X is complex128, else FP32.  Same thread
+// layout as k_combine: CR rows (r, r + 32) by CJ consecutive columns of Q.
 template <typename CX, typename CQ>
-__global__ void k_orth(const CX* __restrict__ X, int m, BlockList<CQ> Q, size_t ld,
-                       const double2* __restrict__ cfs) {
+__global__ void __launch_bounds__(kCombineThreads) k_orth(const CX* __restrict__ X, int m, BlockList<CQ> Q,
+                                                          size_t ld, const double2* __restrict__ cfs) {
     using R = typename Acc<CX>::T;
     using C = CX;
     using RQ = typename Acc<CQ>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nq = Q.total;
-    C* sc = reinterpret_cast<C*>(smem_raw);
-    for (int e = threadIdx.x; e < m * nq; e += blockDim.x) sc[e] = mk((R)cfs[e].x, (R)cfs[e].y);
+    const int nq = Q.total, ng = (nq + CJ - 1) / CJ, MP = ng * CJ;
+    C* sc = reinterpret_cast<C*>(smem_raw);                          // [m][MP]
+    CQ** qp = reinterpret_cast<CQ**>(sc + (size_t)m * MP);           // [nq]
+    for (int e = threadIdx.x; e < m * MP; e += blockDim.x) {
+        const int i = e / MP, j = e - i * MP;
+        sc[e] = j < nq ? mk((R)cfs[(size_t)j * m + i].x, (R)cfs[(size_t)j * m + i].y) : mk((R)0, (R)0);
+    }
+    for (int j = threadIdx.x; j < nq; j += blockDim.x) qp[j] = const_cast<CQ*>(col_ptr(Q, j, ld));
     __syncthreads();
-    for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < ld;
-         row += (size_t)gridDim.x * blockDim.x) {
-        constexpr int JC = sizeof(R) == 4 ? 16 : 8;   // output columns per pass over X
-        for (int j0 = 0; j0 < nq; j0 += JC) {
-            const int jn = min(JC, nq - j0);
-            C a[JC];
+    constexpr int TPS = kCombineThreads / kCombineSlots;
+    const int slot = threadIdx.x / TPS, lt = threadIdx.x % TPS;
+    const size_t span = (size_t)TPS * CR;
+    for (size_t base = blockIdx.x * span; base < ld; base += (size_t)gridDim.x * span) {
+        const size_t ra = base + (size_t)(lt >> 5) * 64 + (lt & 31), rb = ra + 32;
+        const bool va = ra < ld, vb = rb < ld;
+        for (int g = slot; g < ng; g += kCombineSlots) {
+            // start from Q (loads in flight while the products accumulate)
+            C a[CR][CJ];
 #pragma unroll
-            for (int b = 0; b < JC; ++b) a[b] = mk((R)0, (R)0);
+            for (int j = 0; j < CJ; ++j) {
+                const int jj = g * CJ + j;
+#pragma unroll
+                for (int r = 0; r < CR; ++r) {
+                    const size_t row = r == 0 ? ra : rb;
+                    if (jj < nq && row < ld) {
+                        const CQ v = qp[jj][row];
+                        a[r][j] = mk((R)v.x, (R)v.y);
+                    } else {
+                        a[r][j] = mk((R)0, (R)0);
+                    }
+                }
+            }
+            const C* cf = sc + g * CJ;
+#pragma unroll 4
             for (int i = 0; i < m; ++i) {
-                const C x = X[(size_t)i * ld + row];
+                const C xa = va ? X[(size_t)i * ld + ra] : mk((R)0, (R)0);
+                const C xb = vb ? X[(size_t)i * ld + rb] : mk((R)0, (R)0);
 #pragma unroll
-                for (int b = 0; b < JC; ++b)
-                    if (b < jn) a[b] = a[b] + cmul(x, sc[(size_t)(j0 + b) * m + i]);
+                for (int j = 0; j < CJ; ++j) {
+                    const C w = cf[(size_t)i * MP + j];
+                    a[0][j] = a[0][j] - cmul(xa, w);
+                    a[1][j] = a[1][j] - cmul(xb, w);
+                }
             }
 #pragma unroll
-            for (int b = 0; b < JC; ++b) {
-                if (b < jn) {
-                    CQ* q = const_cast<CQ*>(col_ptr(Q, j0 + b, ld)) + row;
-                    const CQ v = *q;
-                    *q = mk((RQ)((R)v.x - a[b].x), (RQ)((R)v.y - a[b].y));
+            for (int j = 0; j < CJ; ++j) {
+                const int jj = g * CJ + j;
+                if (jj >= nq) break;
+#pragma unroll
+                for (int r = 0; r < CR; ++r) {
+                    const size_t row = r == 0 ? ra : rb;
+                    if (row < ld) qp[jj][row] = mk((RQ)a[r][j].x, (RQ)a[r][j].y);
                 }
             }
         }
@@ -466,6 +613,22 @@ __global__ void k_random(C* __restrict__ X, size_t N, uint64_t seed) {
 // ---------------------------------------------------------------------------
 // host wrappers
 // ---------------------------------------------------------------------------
+// Dynamic shared memory limit above the 48 KB default, and the largest shared-memory
+// carveout (so that several blocks fit per SM), set once per kernel.
+fame_status kernel_smem(fame_ctx* c, const void* fn, size_t smem) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find(fn);
+    if (it != done.end() && it->second >= smem) return FAME_OK;
+    if (smem > 48 * 1024)
+        FAME_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FAME_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+    done[fn] = std::max(smem, it != done.end() ? it->second : (size_t)0);
+    return FAME_OK;
+}
+
 template <typename CU, typename CV>
 fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, size_t ld,
                  double2* G, cudaStream_t st) {
@@ -484,9 +647,7 @@ fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, si
     nblk = (int)((ld + rpb - 1) / rpb);
     fame_status s = grow(c, c->partial, (size_t)nblk * ku * kv * sizeof(double2));
     if (s != FAME_OK) return s;
-    if (smem > 48 * 1024)
-        FAME_CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_gram<CU, CV>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if ((s = kernel_smem(c, (const void*)k_gram<CU, CV>, smem)) != FAME_OK) return s;
     double2* part = reinterpret_cast<double2*>(c->partial.p);
     {
         ProfScope ps(K_GRAM, dbl, st, (double)ld * (ku * sizeof(CU) + kv * sizeof(CV)),
@@ -496,7 +657,42 @@ fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, si
     const int kk = ku * kv;
     {
         ProfScope ps(K_GRAM_RED, dbl, st, (double)nblk * kk * sizeof(double2), 2.0 * nblk * kk);
-        k_gram_reduce<<<(kk + 7) / 8, 256, 0, st>>>(part, nblk, kk, G);
+        k_gram_reduce<<<(kk + 7) / 8, 256, 0, st>>>(part, nblk, kk, G, 0);
+    }
+    count_launch(2);
+    FAME_CUDA_TRY(c, cudaGetLastError());
+    return FAME_OK;
+}
+
+template <typename C>
+fame_status gram_herm(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V, size_t ld, double2* G,
+                      cudaStream_t st) {
+    const int ku = U.total;
+    if (V.total != ku) return set_err(c, FAME_E_ARG, "gram_herm: U and V differ in width");
+    const int T = (ku + GT - 1) / GT, tiles = T * (T + 1);
+    const int groups = (tiles + kGramThreads - 1) / kGramThreads;
+    int threads = (((tiles + groups - 1) / groups + 31) / 32) * 32;
+    if (threads < 64) threads = 64;
+    const bool dbl = sizeof(C) == 16;
+    const size_t smem = (size_t)4 * GROWS * herm_stride(ku) * sizeof(C) + (size_t)2 * ku * sizeof(void*);
+    int nblk = 152 * 4;
+    size_t rpb = (ld + nblk - 1) / nblk;
+    rpb = ((rpb + GROWS - 1) / GROWS) * GROWS;
+    nblk = (int)((ld + rpb - 1) / rpb);
+    const int kk = ku * 2 * ku;
+    fame_status s = grow(c, c->partial, (size_t)nblk * kk * sizeof(double2));
+    if (s != FAME_OK) return s;
+    if ((s = kernel_smem(c, (const void*)k_gram_herm<C>, smem)) != FAME_OK) return s;
+    double2* part = reinterpret_cast<double2*>(c->partial.p);
+    {
+        // algorithmic work of the computed entries: about half of the two square blocks
+        const double frac = (double)tiles * GT * GT / (2.0 * ku * ku);
+        ProfScope ps(K_GRAM, dbl, st, (double)ld * 2 * ku * sizeof(C), 8.0 * 2 * ku * ku * frac * (double)ld);
+        k_gram_herm<C><<<dim3(nblk, groups), threads, smem, st>>>(U, V, ld, rpb, part);
+    }
+    {
+        ProfScope ps(K_GRAM_RED, dbl, st, (double)nblk * kk * sizeof(double2), 2.0 * nblk * kk);
+        k_gram_reduce<<<(kk + 7) / 8, 256, 0, st>>>(part, nblk, kk, G, ku);
     }
     count_launch(2);
     FAME_CUDA_TRY(c, cudaGetLastError());
@@ -508,9 +704,8 @@ fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2
                     Co* out1, Co* out2, cudaStream_t st) {
     const int MP = ((m + CJ - 1) / CJ) * CJ;
     const size_t smem = (size_t)S.total * MP * sizeof(C) + (size_t)S.total * sizeof(void*);
-    if (smem > 48 * 1024)
-        FAME_CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_combine<C, Co>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fame_status s = kernel_smem(c, (const void*)k_combine<C, Co>, smem);
+    if (s != FAME_OK) return s;
     {
         const double outs = (out1 ? m : 0) + (out2 ? m : 0);
         ProfScope ps(K_COMBINE, sizeof(C) == sizeof(double2), st,
@@ -558,9 +753,8 @@ fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<
     const int nq = Q.total;
     const int MP = ((m + MJ - 1) / MJ) * MJ;
     const size_t smem = (size_t)m * MP * sizeof(float4) + (size_t)nq * MP * sizeof(float2) + (size_t)nq * sizeof(void*);
-    if (smem > 48 * 1024)
-        FAME_CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_combine_mixed,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fame_status s = kernel_smem(c, (const void*)k_combine_mixed, smem);
+    if (s != FAME_OK) return s;
     {
         ProfScope ps(K_COMBINE, true, st,
                      (double)ld * (m * sizeof(double2) + nq * sizeof(float2) +
@@ -578,13 +772,16 @@ fame_status orth_against(fame_ctx* c, const CX* X, int m, const BlockList<CQ>& Q
                          const double2* cfs, cudaStream_t st) {
     const int nq = Q.total;
     if (nq == 0) return FAME_OK;
-    const size_t smem = (size_t)m * nq * sizeof(CX);
-    if (smem > 48 * 1024)
-        FAME_CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_orth<CX, CQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int MP = ((nq + CJ - 1) / CJ) * CJ;
+    const size_t smem = (size_t)m * MP * sizeof(CX) + (size_t)nq * sizeof(void*);
+    fame_status s = kernel_smem(c, (const void*)k_orth<CX, CQ>, smem);
+    if (s != FAME_OK) return s;
     {
         ProfScope ps(K_COMBINE, sizeof(CX) == 16, st, (double)ld * (m * sizeof(CX) + 2 * nq * sizeof(CQ)),
                      8.0 * (double)ld * m * nq);
-        k_orth<CX, CQ><<<152 * 8, 256, smem, st>>>(X, m, Q, ld, cfs);
+        const size_t span = (size_t)(kCombineThreads / kCombineSlots) * CR;
+        const unsigned nblk = (unsigned)std::min<size_t>(152 * 4, (ld + span - 1) / span);
+        k_orth<CX, CQ><<<nblk, kCombineThreads, smem, st>>>(X, m, Q, ld, cfs);
     }
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
@@ -622,6 +819,8 @@ fame_status mask_block(fame_ctx* c, C* X, int m, const typename RealOf<C>::T* ti
     return FAME_OK;
 }
 
+template fame_status gram_herm<float2>(fame_ctx*, const BlockList<float2>&, const BlockList<float2>&, size_t, double2*, cudaStream_t);
+template fame_status gram_herm<double2>(fame_ctx*, const BlockList<double2>&, const BlockList<double2>&, size_t, double2*, cudaStream_t);
 template fame_status gram<float2, float2>(fame_ctx*, const BlockList<float2>&, const BlockList<float2>&, size_t, double2*, cudaStream_t);
 template fame_status gram<double2, double2>(fame_ctx*, const BlockList<double2>&, const BlockList<double2>&, size_t, double2*, cudaStream_t);
 template fame_status gram<double2, float2>(fame_ctx*, const BlockList<double2>&, const BlockList<float2>&, size_t, double2*, cudaStream_t);

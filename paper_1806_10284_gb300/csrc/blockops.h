@@ -47,6 +47,11 @@ template <> struct RealOf<double2> { using T = double; };
 template <typename CU, typename CV>
 fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, size_t ld, double2* G,
                  cudaStream_t st);
+// G (column-major k x 2k) = [U^H U | U^H V] for V = A U with A Hermitian: only the
+// entries on or below the diagonal of each k x k block are computed (the others are 0)
+template <typename C>
+fame_status gram_herm(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V, size_t ld, double2* G,
+                      cudaStream_t st);
 // out1 = S M[:, :m], out2 = S[:, i0:] M[i0:, :m]  (either output may be null)
 template <typename C, typename Co>
 fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2* M, int m, int i0,

@@ -257,8 +257,8 @@ fame_status lob_explicit(fame_ctx* c, C* const S[2], C* const AS[2], const Small
         const int k = m + nw + np;
         const BlockList<C> U = blocks<C>(X, m, Wb, nw, Pb, np);
         const BlockList<C> V = blocks<C>(AX, m, AWb, nw, APb, np);
-        // [GB | GA] = U^H [U | V] in one pass over U
-        if ((s = gram<C, C>(c, U, concat(U, V), ld, sm.G, st)) != FAME_OK) return s;
+        // [GB | GA] = U^H [U | V] in one pass over U; lower triangles only (both Hermitian)
+        if ((s = gram_herm<C>(c, U, V, ld, sm.G, st)) != FAME_OK) return s;
         std::vector<double> th;
         const int got = host_rr(c, sm, k, m, 0, theta, drop, th, Cm, st, &s);
         if (got < 0) return s;

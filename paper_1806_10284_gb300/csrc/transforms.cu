@@ -419,13 +419,21 @@ __global__ void __launch_bounds__(256) k_xpass(KParams<R> P, typename cpx<R>::T*
     for (int e = threadIdx.x; e < nr * n1; e += blockDim.x) g[e] = cur[e];
 }
 
-// dB[i] += -w |x[i]|^2 over the three components of one lifted vector
-__global__ void k_grad_accum(const double2* __restrict__ x, double w, double* __restrict__ dB,
-                             size_t N) {
+// weights of up to kGradChunk lifted bands
+constexpr int kGradChunk = 16;
+struct GradWeights { double w[kGradChunk]; };
+
+// dB[i] -= sum_j w_j |x_j[i]|^2 over mc lifted vectors x_j ([mc][3][n], N = 3n)
+__global__ void k_grad_accum(const double2* __restrict__ x, GradWeights w, int mc,
+                             double* __restrict__ dB, size_t N) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
          i += (size_t)gridDim.x * blockDim.x) {
-        const double2 v = x[i];
-        dB[i] -= w * (v.x * v.x + v.y * v.y);
+        double acc = 0.0;
+        for (int j = 0; j < mc; ++j) {
+            const double2 v = x[(size_t)j * N + i];
+            acc += w.w[j] * (v.x * v.x + v.y * v.y);
+        }
+        dB[i] -= acc;
     }
 }
 
@@ -916,16 +924,25 @@ fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::
 fame_status run_grad(fame_ctx* c, const double2* Y, const double* w, int nev, double* dB,
                      cudaStream_t st) {
     const size_t N = 3 * (size_t)c->n;
-    fame_status s = grow(c, c->work, N * sizeof(double2));
+    // bands lifted together, the workspace kept near 1 GiB at most
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(kGradChunk, ((size_t)1 << 30) / (N * sizeof(double2))));
+    fame_status s = grow(c, c->work, (size_t)chunk * N * sizeof(double2));
     if (s != FAME_OK) return s;
-    double2* x = reinterpret_cast<double2*>(c->work.p);   // lifted band, [3][n]
+    double2* x = reinterpret_cast<double2*>(c->work.p);   // lifted bands, [chunk][3][n]
     FAME_CUDA_TRY(c, cudaMemsetAsync(dB, 0, N * sizeof(double), st));
-    for (int j = 0; j < nev; ++j) {
-        if (w[j] == 0.0) continue;
-        if ((s = run_lift<double>(c, Y + (size_t)j * 2 * c->n, x, 1, st)) != FAME_OK) return s;
+    for (int j0 = 0; j0 < nev; j0 += chunk) {
+        const int mc = std::min(chunk, nev - j0);
+        GradWeights gw{};
+        bool any = false;
+        for (int j = 0; j < mc; ++j) {
+            gw.w[j] = w[j0 + j];
+            any = any || w[j0 + j] != 0.0;
+        }
+        if (!any) continue;
+        if ((s = run_lift<double>(c, Y + (size_t)j0 * 2 * c->n, x, mc, st)) != FAME_OK) return s;
         {
-            ProfScope ps(K_GRAD, true, st, (double)N * (sizeof(double2) + 2 * sizeof(double)), 4.0 * N);
-            k_grad_accum<<<1216, 256, 0, st>>>(x, w[j], dB, N);
+            ProfScope ps(K_GRAD, true, st, (double)N * (mc * sizeof(double2) + 2 * sizeof(double)), 4.0 * N * mc);
+            k_grad_accum<<<1216, 256, 0, st>>>(x, gw, mc, dB, N);
         }
         count_launch();
         FAME_CUDA_TRY(c, cudaGetLastError());
