@@ -192,11 +192,11 @@ def _bound(name):
         hbm, kind = measured_peaks()
         return "hbm", hbm, "GB/s", (f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured"
                                     else "fallback 6.8 TB/s")
+    if base == "combine_df":
+        return "alu", FP32_PEAK_TFLOPS, "TFLOP/s", ("FP32 lanes x clock (recipe table: 152 SMs, 2.07 GHz); "
+                                                    "double-float sums on FP32 units, flops = FP32 operations")
     if prec == "c128":
-        src = "nominal FP64 rate (recipe table)"
-        if base == "combine":
-            src += "; this kernel sums in double-float on the FP32 units"
-        return "alu", FP64_PEAK_TFLOPS, "TFLOP/s", src
+        return "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "nominal FP64 rate (recipe table)"
     return "alu", FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 lanes x clock (recipe table: 152 SMs, 2.07 GHz)"
 
 

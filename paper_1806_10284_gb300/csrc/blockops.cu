@@ -685,9 +685,8 @@ fame_status gram_herm(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V,
     if ((s = kernel_smem(c, (const void*)k_gram_herm<C>, smem)) != FAME_OK) return s;
     double2* part = reinterpret_cast<double2*>(c->partial.p);
     {
-        // algorithmic work of the computed entries: about half of the two square blocks
-        const double frac = (double)tiles * GT * GT / (2.0 * ku * ku);
-        ProfScope ps(K_GRAM, dbl, st, (double)ld * 2 * ku * sizeof(C), 8.0 * 2 * ku * ku * frac * (double)ld);
+        // algorithmic work: the ku (ku + 1) entries on or below the two diagonals
+        ProfScope ps(K_GRAM_HERM, dbl, st, (double)ld * 2 * ku * sizeof(C), 8.0 * ku * (ku + 1) * (double)ld);
         k_gram_herm<C><<<dim3(nblk, groups), threads, smem, st>>>(U, V, ld, rpb, part);
     }
     {
@@ -709,7 +708,7 @@ fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2
     {
         const double outs = (out1 ? m : 0) + (out2 ? m : 0);
         ProfScope ps(K_COMBINE, sizeof(C) == sizeof(double2), st,
-                     (double)S.total * ld * sizeof(C) + outs * ld * sizeof(Co), 8.0 * S.total * outs * (double)ld);
+                     (double)S.total * ld * sizeof(C) + outs * ld * sizeof(Co), 8.0 * S.total * m * (double)ld);
         const size_t span = (size_t)(kCombineThreads / kCombineSlots) * CR;
         const unsigned nblk = (unsigned)std::min<size_t>(152 * 4, (ld + span - 1) / span);
         k_combine<C, Co><<<nblk, kCombineThreads, smem, st>>>(S, ld, M, m, i0, out1, out2);
@@ -756,10 +755,13 @@ fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<
     fame_status s = kernel_smem(c, (const void*)k_combine_mixed, smem);
     if (s != FAME_OK) return s;
     {
-        ProfScope ps(K_COMBINE, true, st,
+        // FP32 operations of the double-float algorithm: per complex X coefficient four
+        // double-float products (one multiply, three FMAs, a six-operation two-sum and two
+        // adds: 15 flops counting an FMA as two), plus complex64 MACs (8 flops) for Q
+        ProfScope ps(K_COMBINE_DF, true, st,
                      (double)ld * (m * sizeof(double2) + nq * sizeof(float2) +
                                    m * (sizeof(double2) + sizeof(float2) + (Pn ? sizeof(float2) : 0))),
-                     8.0 * (double)ld * m * (m + nq));
+                     (double)ld * m * (4.0 * 15.0 * m + 8.0 * nq));
         k_combine_mixed<<<152 * 8, 256, smem, st>>>(X, m, Q, ld, M, Xn, X32n, Pn);
     }
     count_launch();
@@ -777,7 +779,7 @@ fame_status orth_against(fame_ctx* c, const CX* X, int m, const BlockList<CQ>& Q
     fame_status s = kernel_smem(c, (const void*)k_orth<CX, CQ>, smem);
     if (s != FAME_OK) return s;
     {
-        ProfScope ps(K_COMBINE, sizeof(CX) == 16, st, (double)ld * (m * sizeof(CX) + 2 * nq * sizeof(CQ)),
+        ProfScope ps(K_ORTH, sizeof(CX) == 16, st, (double)ld * (m * sizeof(CX) + 2 * nq * sizeof(CQ)),
                      8.0 * (double)ld * m * nq);
         const size_t span = (size_t)(kCombineThreads / kCombineSlots) * CR;
         const unsigned nblk = (unsigned)std::min<size_t>(152 * 4, (ld + span - 1) / span);

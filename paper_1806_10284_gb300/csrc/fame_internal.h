@@ -149,7 +149,7 @@ void count_launch(int k = 1);
 
 // kernel kinds for the opt-in profiler (profile.cpp)
 enum KernelKind { K_ZIN, K_XY, K_ZOUT, K_YPASS, K_XPASS, K_GRAM, K_GRAM_RED, K_COMBINE, K_RESID,
-                  K_CONVERT, K_GRAD, K_SETUP, K_COUNT };
+                  K_CONVERT, K_GRAD, K_SETUP, K_GRAM_HERM, K_ORTH, K_COMBINE_DF, K_COUNT };
 // Brackets a launch with events on its stream when profiling is on; attaches the
 // launch's algorithmic bytes and flops.
 class ProfScope {
