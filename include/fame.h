@@ -234,15 +234,21 @@ FAME_API fame_status fame_grad_eps(fame_ctx* ctx, int nev, const double* dobj_dl
                           double* dB_out, void* stream);
 
 /*
- * fame_eigs_batched -- solve several contexts (lattices and Bloch vectors,
- * grids may differ) in lock-step: each LOBPCG iteration of every problem is
- * one captured CUDA graph replay; problems that converge drop out.
- *   ctxs       : host array of nprob context pointers (eps set on each).
+ * fame_eigs_batched -- solve several contexts (lattices and Bloch vectors along
+ * band paths, grids may differ), several problems in flight at once: four
+ * host worker threads with their own streams take problems in order, so the
+ * GPU runs one problem's kernels while another waits for its host
+ * Rayleigh-Ritz step.  Each worker lends one transform/solver workspace to the
+ * problems it solves (device memory grows with the workers, not the batch);
+ * every context keeps its eigenvectors as after fame_eigs.  The work starts
+ * after the work already queued on stream.
+ *   ctxs       : host array of nprob distinct context pointers (eps set on each).
  *   nev, tol, max_iter, flags : as fame_eigs (FAME_MIXED or FAME_FP64).
  *   lambda_out : host [nprob][nev] doubles.
  *   iters_out  : host [nprob] ints, or NULL.
- * Synchronises stream.  Errors: as fame_eigs; FAME_E_NOCONV if any problem
- * did not converge.
+ * Returns when every problem is done.  Errors: as fame_eigs (the first failing
+ * problem's status; its context holds the message); FAME_E_ARG for a repeated
+ * context; FAME_E_NOCONV if any problem did not converge.
  */
 FAME_API fame_status fame_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol,
                               int max_iter, int flags, double* lambda_out, int* iters_out,

@@ -286,8 +286,11 @@ fame_status fame_grad_eps(fame_ctx* c, int nev, const double* dobj, double rel_c
 fame_status fame_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol, int max_iter,
                               int flags, double* lambda_out, int* iters_out, void* stream) {
     if (!ctxs || nprob < 1 || !lambda_out) return set_err(nullptr, FAME_E_ARG, "bad batch arguments");
-    for (int i = 0; i < nprob; ++i)
+    for (int i = 0; i < nprob; ++i) {
         if (!ctxs[i]) return set_err(nullptr, FAME_E_ARG, "null context in batch");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return set_err(nullptr, FAME_E_ARG, "context repeated in batch");
+    }
     return run_eigs_batched(ctxs, nprob, nev, tol, max_iter, flags, lambda_out, iters_out,
                             static_cast<cudaStream_t>(stream));
 }

@@ -24,9 +24,12 @@
 //            reported residuals ||A_r y - lambda y|| / lambda come from it.
 // FAME_FP64: complex128 blocks throughout, explicit FP64 Gram matrices.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include "blockops.h"
@@ -542,16 +545,81 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
     return FAME_OK;
 }
 
+// Several problems in flight at once: kBatchWorkers host threads, each with its own
+// non-blocking stream, take problems from a shared counter.  While one problem waits
+// for its host Rayleigh-Ritz step the GPU runs the others' kernels.  A worker lends
+// its own workspace to each problem it solves, so device memory grows with the
+// number of workers, not with the number of problems.
+namespace {
+constexpr int kBatchWorkers = 4;
+
+struct BatchWorkspace {
+    GrowBuf work, solver, solver2, partial;
+};
+
+void lend(fame_ctx* c, BatchWorkspace& w) {
+    std::swap(c->work, w.work);
+    std::swap(c->solver, w.solver);
+    std::swap(c->solver2, w.solver2);
+    std::swap(c->partial, w.partial);
+}
+
+void release(BatchWorkspace& w) {
+    for (GrowBuf* b : {&w.work, &w.solver, &w.solver2, &w.partial})
+        if (b->p) cudaFree(b->p);
+}
+}  // namespace
+
 fame_status run_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol, int max_iter,
                              int flags, double* lambda_out, int* iters_out, cudaStream_t st) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_err(nullptr, FAME_E_CUDA, "cudaGetDevice");
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (ready) cudaEventDestroy(ready);
+        return set_err(nullptr, FAME_E_CUDA, "batch: event on the caller's stream");
+    }
+    const int workers = std::min(nprob, kBatchWorkers);
+    std::atomic<int> next(0);
+    std::vector<fame_status> status(nprob, FAME_OK);
+    std::vector<fame_status> wstatus(workers, FAME_OK);
+    std::vector<std::thread> pool;
+    for (int w = 0; w < workers; ++w) {
+        pool.emplace_back([&, w] {
+            cudaStream_t ws = nullptr;
+            if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) {
+                cudaGetLastError();
+                wstatus[w] = FAME_E_CUDA;
+                if (ws) cudaStreamDestroy(ws);
+                return;
+            }
+            BatchWorkspace bw;
+            for (;;) {
+                const int i = next.fetch_add(1);
+                if (i >= nprob) break;
+                fame_ctx* c = ctxs[i];
+                lend(c, bw);
+                int it = 0;
+                status[i] = fame_eigs(c, nev, tol, max_iter, flags, lambda_out + (size_t)i * nev, nullptr, &it, ws);
+                lend(c, bw);                  // the context gets its own buffers back
+                if (iters_out) iters_out[i] = it;
+            }
+            if (cudaStreamSynchronize(ws) != cudaSuccess) wstatus[w] = FAME_E_CUDA;
+            release(bw);
+            cudaStreamDestroy(ws);
+        });
+    }
+    for (auto& t : pool) t.join();
+    cudaEventDestroy(ready);
+    for (int w = 0; w < workers; ++w)
+        if (wstatus[w] != FAME_OK) return set_err(nullptr, wstatus[w], "batch: worker stream setup failed");
     fame_status worst = FAME_OK;
     for (int i = 0; i < nprob; ++i) {
-        int it = 0;
-        fame_status s = fame_eigs(ctxs[i], nev, tol, max_iter, flags, lambda_out + (size_t)i * nev,
-                                  nullptr, &it, st);
-        if (iters_out) iters_out[i] = it;
-        if (s == FAME_E_NOCONV) worst = s;
-        else if (s != FAME_OK) return s;
+        if (status[i] == FAME_E_NOCONV) worst = FAME_E_NOCONV;
+        else if (status[i] != FAME_OK) return status[i];
     }
     return worst;
 }

@@ -313,7 +313,9 @@ def eigs_batched(contexts, nev, tol=1e-8, max_iter=400, flags=FAME_MIXED, stream
     st = lib.fame_eigs_batched(arr, len(contexts), int(nev), float(tol), int(max_iter), int(flags),
                                lam.ctypes.data_as(_D3), its, _stream(stream))
     if st != 0:
-        raise FameError(st, "batched solve failed")
+        msgs = [lib.fame_last_error(c._h) for c in contexts]
+        msg = next((m.decode() for m in msgs if m), None) or (lib.fame_last_error(None) or b"").decode()
+        raise FameError(st, msg or "batched solve failed")
     return lam, list(its)
 
 

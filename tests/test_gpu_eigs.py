@@ -210,3 +210,22 @@ def test_fcc64_full_size_against_oracle_golden(flags, rtol):
         r = apply_Ar(lat, y, invB).ravel() - lam[j] * Yh[j]
         assert np.linalg.norm(r) <= 1.05e-8 * lam[j] * np.linalg.norm(Yh[j])
     ctx.close()
+
+
+def test_batched_matches_individual_and_dense():
+    """fame_eigs_batched (several problems in flight on worker streams) gives the same
+    eigenvalues as one fame_eigs per context, and the dense oracle's."""
+    probs = []
+    for name, n in (("fcc64", (6, 6, 6)), ("tri192", (8, 6, 5)), ("hex96", (8, 8, 5))):
+        for seed in (3, 4):
+            probs.append(_small(name, n, seed=seed))
+    ctxs = [p[1] for p in probs]
+    lam_b, its = fame.eigs_batched(ctxs, 8, tol=1e-10, flags=fame.FAME_MIXED)
+    assert all(i > 0 for i in its)
+    for (lat, ctx, B), lb in zip(probs, lam_b):
+        lam_1 = ctx.eigs(8, tol=1e-10, flags=fame.FAME_MIXED)[0]
+        np.testing.assert_allclose(lb, lam_1, rtol=1e-12)
+        ref, _ = eigs_dense(lat, 1.0 / B, 8)
+        np.testing.assert_allclose(lb, ref, rtol=1e-9)
+    with pytest.raises(fame.FameError):
+        fame.eigs_batched([ctxs[0], ctxs[0]], 8)
