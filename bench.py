@@ -11,6 +11,12 @@ eigensolve part of a step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+After the timed steps (outside the timed region) a single-GPU run also reports
+the plain FP64 solve of the same problem (``fp64_time_to_10_bands_s``) and a
+band-path batch on the BCC, hexagonal and monoclinic workloads solved one
+problem after another and as one concurrent ``fame_eigs_batched`` call
+(``band_path``); ``--no-extras`` skips both.
+
 Under torchrun each rank solves its own Bloch vector (independent problems,
 no data-path collective: weak scaling).  ``--impl reference`` times the CPU
 oracle (FP64 numpy) on bounded samples of the same workload.
@@ -48,6 +54,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-FP64 solve and the band-path batch after the timed steps")
     return ap.parse_args()
 
 
@@ -162,14 +170,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FFT_PASSES = ("zin", "xy", "zout", "ypass", "xpass")
 
 
+KERNEL_SOURCES = ("apply3.cu", "blockops.cu", "transforms.cu", "eps.cu", "noalloc.cu", "fft2.cuh",
+                  "phases.cuh", "df64.cuh", "fame_internal.h", "blockops.h")
+
+
 def kernel_source_hash():
-    """Hash of every CUDA source file: committed DRAM counters are used only while it matches."""
+    """Hash of the files that define device code: committed DRAM counters are used only
+    while it matches."""
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_1806_10284_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(src, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(f.encode())
+        h.update(open(os.path.join(src, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -226,6 +238,58 @@ def apply_roofline(prof):
     t = sum(v["total_ms"] for v in parts) / 1e3
     return {"bound": "hbm", "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": b / t / 1e9 / hbm, "bytes_model": "16 n complex64 per vector + 3 n B^{-1} per block"}
+
+
+# ---------------------------------------------------------------------------
+# comparisons reported beside the timed steps (not part of the timed region)
+# ---------------------------------------------------------------------------
+BAND_PATH = ("bcc96", "hex96", "mono80")
+
+
+def comparisons(ctx, lam_mixed, k_per_lattice=2):
+    """The plain FP64 solve of the bench problem, and a band-path batch (BCC 96^3,
+    hexagonal 96x96x80, monoclinic 80x96x64; k_per_lattice Bloch vectors each) solved
+    one problem after another and as one concurrent batch."""
+    import torch
+    from paper_1806_10284_gb300 import fame
+    from paper_1806_10284_gb300 import workloads as W
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    lam64, _, it64 = ctx.eigs(NEV, tol=TOL, max_iter=800, flags=fame.FAME_FP64)
+    e1.record()
+    torch.cuda.synchronize()
+    res = {"fp64_time_to_10_bands_s": e0.elapsed_time(e1) / 1e3, "fp64_iterations": int(it64),
+           "fp64_vs_mixed_max_rel": float(np.max(np.abs(lam64 - lam_mixed) / np.abs(lam64)))}
+    ctxs = []
+    for name in BAND_PATH:
+        w = W.WORKLOADS[name]
+        Ks = W.bloch_vectors(name)
+        eps = None
+        for i in np.linspace(1, len(Ks) - 2, k_per_lattice).astype(int):
+            c = fame.Context(w["vectors"], w["n"], Ks[i])
+            if eps is None:
+                eps = W.eps_for(name, c.geometry())
+            c.set_eps(*eps)
+            ctxs.append(c)
+    ctxs[0].eigs(NEV, tol=TOL, flags=fame.FAME_MIXED)      # first-use allocations
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [c.eigs(NEV, tol=TOL, flags=fame.FAME_MIXED)[0] for c in ctxs]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lam_b, its = fame.eigs_batched(ctxs, NEV, tol=TOL, flags=fame.FAME_MIXED)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    res["band_path"] = {
+        "lattices": list(BAND_PATH), "k_per_lattice": k_per_lattice, "problems": len(ctxs),
+        "bands": NEV, "residual": TOL, "sequential_s": t_seq, "batched_s": t_b,
+        "batched_per_problem_s": t_b / len(ctxs), "iterations": [int(i) for i in its],
+        "batched_vs_sequential_max_rel": float(max(np.max(np.abs(a - b) / np.abs(b)) for a, b in zip(lam_b, seq)))}
+    for c in ctxs:
+        c.close()
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -357,6 +421,9 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.all_reduce(a, op=dist.ReduceOp.SUM)
         e2e_s, e2e_applies = float(t[0]), int(a[0])
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = comparisons(ctx, lam)
     if rank != 0:
         return
     rl = roofline(prof)
@@ -388,6 +455,8 @@ def run_ours(args, rank, world, local):
                    "h2d_bytes_per_step": int(3 * ctx.N * 8),
                    "d2h_bytes_per_step": int(NEV * 8 + 3 * ctx.N * 8)},
            "cpu_baseline": cpu}
+    if extras:
+        out.update(extras)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
