@@ -34,6 +34,7 @@ CASES = [
     ("mono80", (48, 48, 32)),    # XY 48x48, Z 32
     ("hex96", (20, 32, 16)),     # Z 16 with a ragged x tile, generic XY
     ("bcc96", (80, 96, 16)),     # XY 80x96
+    ("tri192", (128, 128, 4)),   # plane too large for shared memory: split y / x / y passes
 ]
 
 
@@ -163,9 +164,11 @@ def test_set_k_rebuilds_twists():
     assert _rel(got, ref) < TOL64
 
 
-@pytest.mark.parametrize("name", ["fcc64", "bcc96", "hex96", "mono80"])
-def test_homogeneous_closed_form_full_size(name):
-    """B = c: A_r y = (Lambda_q / c) y at the workload's full grid, in the bench's block size."""
+@pytest.mark.parametrize("name,m", [("fcc64", 16), ("bcc96", 16), ("hex96", 16), ("mono80", 16),
+                                    ("tri192", 4)])
+def test_homogeneous_closed_form_full_size(name, m):
+    """B = c: A_r y = (Lambda_q / c) y at the workload's full grid (192^3 takes the split
+    y / x / y passes), m vectors per block."""
     w = W.WORKLOADS[name]
     K = W.bloch_vectors(name)[0]
     lat = make_lattice(w["vectors"], w["n"], K)
@@ -176,7 +179,6 @@ def test_homogeneous_closed_form_full_size(name):
     Lq = (bases(lat)[3] ** 2).ravel()
     lam = np.concatenate([Lq, Lq]) / c
     g = torch.Generator(device="cuda").manual_seed(0)
-    m = 16
     y = torch.randn((m, 2 * lat.n), dtype=torch.complex128, device="cuda", generator=g)
     lam_t = torch.as_tensor(lam, device="cuda")
     for dt, tol in ((torch.complex128, TOL64), (torch.complex64, TOL32)):

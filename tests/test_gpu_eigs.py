@@ -229,3 +229,49 @@ def test_batched_matches_individual_and_dense():
         np.testing.assert_allclose(lb, ref, rtol=1e-9)
     with pytest.raises(fame.FameError):
         fame.eigs_batched([ctxs[0], ctxs[0]], 8)
+
+
+@pytest.mark.parametrize("flags", [fame.FAME_MIXED, fame.FAME_FP64])
+def test_config_sc48_band_gap_gradient(flags):
+    """The differentiable band-gap workload at full size: SC 48^3, smooth eps on grid nodes,
+    B_l the mean of each Yee edge's two end nodes; obj = sum over two of its Bloch vectors of
+    (lambda_6 - lambda_5) / lambda_5.  d obj / d eps at node voxels from the adjoint gradient
+    (chain rule through the edge means) against central differences (step 1e-4)."""
+    w = W.WORKLOADS["sc48grad"]
+    eps0, _ = W.smooth_field_eps(w["n"], w["seed"])
+    Ks = W.bloch_vectors("sc48grad")[:2]
+    ctxs = [fame.Context(w["vectors"], w["n"], K) for K in Ks]
+
+    def edges(e):
+        return [0.5 * (e + np.roll(e, -1, axis=2)), 0.5 * (e + np.roll(e, -1, axis=1)),
+                0.5 * (e + np.roll(e, -1, axis=0))]
+
+    def objective(e, grad):
+        B = edges(e)
+        total, g = 0.0, np.zeros_like(e)
+        for ctx in ctxs:
+            ctx.set_eps(*B)
+            lam = ctx.eigs(6, tol=1e-10, flags=flags)[0]
+            total += (lam[5] - lam[4]) / lam[4]
+            if grad:
+                d = np.zeros(6)
+                d[5], d[4] = 1.0 / lam[4], -lam[5] / lam[4] ** 2
+                gB = ctx.grad(6, d, rel_cluster=1e-8).cpu().numpy().reshape((3,) + e.shape)
+                g += 0.5 * (gB[0] + np.roll(gB[0], 1, axis=2)) + 0.5 * (gB[1] + np.roll(gB[1], 1, axis=1)) \
+                    + 0.5 * (gB[2] + np.roll(gB[2], 1, axis=0))
+        return total, g
+
+    _, g = objective(eps0, True)
+    rng = np.random.default_rng(404)
+    h = 1e-4
+    for _ in range(4):
+        v = tuple(int(rng.integers(0, s)) for s in eps0.shape)
+        vals = []
+        for sgn in (1, -1):
+            e = eps0.copy()
+            e[v] += sgn * h
+            vals.append(objective(e, False)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert g[v] == pytest.approx(fd, rel=2e-4, abs=1e-9), (v, g[v], fd)
+    for ctx in ctxs:
+        ctx.close()
