@@ -37,19 +37,94 @@ template <int L> struct Sp {
     static constexpr int RMAX = R1 > R2 ? R1 : R2;
 };
 // Z-pass blocks per SM asked of the register allocator: about 640 resident threads
-// where that fits without spills (the radix 8 x 8 and shorter splits), else about 512
-template <int L, int NT> struct ZOcc {
-    static constexpr int threads = (L == 64 || L <= 32) ? 640 : 512;
+// where that fits without spills, else about 512
+template <int L, int NT, bool OUT> struct ZOcc {
+    static constexpr int threads = ((L == 64 && !OUT) || L <= 32) ? 640 : 512;
     static constexpr int value = threads / NT > 0 ? threads / NT : 1;
 };
 
-// x * w_L^{j}, w_L = e^{-2 pi i/L}, conjugated for an inverse transform; tw holds w_L^j
+// x * w_L^{t k}, w_L = e^{-2 pi i/L}, conjugated for an inverse transform; tw holds w_L^j.
+// k is a compile-time index in the callers' unrolled loops (k = 0: no factor); t = 0
+// multiplies by tw[0] = 1 exactly.
 template <bool INV, typename C>
-__device__ __forceinline__ C twid(C x, const C* tw, int j) {
-    if (j == 0) return x;
-    C w = tw[j];
+__device__ __forceinline__ C twid(C x, const C* tw, int t, int k) {
+    if (k == 0) return x;
+    C w = tw[t * k];
     if (INV) w.y = -w.y;
     return cmul(x, w);
+}
+
+// Per-pencil parts of the range basis (one x-frequency p at one y-frequency q):
+// Lambda_1, Lambda_2, |Lambda_1|^2 + |Lambda_2|^2, and the partial sums
+// Lambda_1 + Lambda_2, Lambda_1 - Lambda_2 of e.Lambda for the two reference
+// vectors e = (1,1,1) and e = (1,-1,0).
+template <typename R>
+struct PencilBasis {
+    typename cpx<R>::T L0, L1, S01, D01;
+    R P01;
+};
+
+// (o_0, o_1, o_2) = Sigma_r [Pi_1 Pi_2] (y1, y2) at one frequency, eqs. (range_basis1),
+// (range_basis2), (SVD) written out: with g = |e|^2 Lq - |e.Lambda|^2 and x = e x Lambda,
+//   o_l = g^{-1/2} [ (Lq e_l - Lambda_l conj(e.Lambda)) y1 + Lq^{1/2} conj(x_l) y2 ].
+template <typename R>
+__device__ __forceinline__ void expand(const PencilBasis<R>& b, typename cpx<R>::T L2, bool alt,
+                                       typename cpx<R>::T y1, typename cpx<R>::T y2,
+                                       typename cpx<R>::T& o0, typename cpx<R>::T& o1,
+                                       typename cpx<R>::T& o2) {
+    using C = typename cpx<R>::T;
+    const R Lq = b.P01 + L2.x * L2.x + L2.y * L2.y;
+    if (!(Lq > (R)0)) {
+        o0 = o1 = o2 = mk((R)0, (R)0);
+        return;
+    }
+    C ed, x0, x1, x2;
+    R een, e1, e2;
+    if (!alt) {
+        ed = b.S01 + L2; x0 = L2 - b.L1; x1 = b.L0 - L2; x2 = b.L1 - b.L0; een = 3; e1 = 1; e2 = 1;
+    } else {
+        ed = b.D01; x0 = mk(-L2.x, -L2.y); x1 = x0; x2 = b.S01; een = 2; e1 = -1; e2 = 0;
+    }
+    const R r2 = rsq(een * Lq - (ed.x * ed.x + ed.y * ed.y));
+    const R sr = root(Lq) * r2;
+    const C u = r2 * y1, v = sr * y2;
+    const C d = cmulc(ed, u);                        // conj(e.Lambda) u
+    const C w = Lq * u;
+    o0 = w - cmul(b.L0, d) + cmulc(x0, v);
+    o1 = e1 * w - cmul(b.L1, d) + cmulc(x1, v);
+    o2 = e2 * w - cmul(L2, d) + cmulc(x2, v);
+}
+
+// The adjoint: (z1, z2) = Sigma_r [Pi_1 Pi_2]^H (W_0, W_1, W_2) at one frequency,
+//   z1 = g^{-1/2} [ Lq e.W - (e.Lambda) conj(Lambda).W ],  z2 = g^{-1/2} Lq^{1/2} x.W.
+template <typename R>
+__device__ __forceinline__ void contract(const PencilBasis<R>& b, typename cpx<R>::T L2, bool alt,
+                                         typename cpx<R>::T W0, typename cpx<R>::T W1,
+                                         typename cpx<R>::T W2, typename cpx<R>::T& z1,
+                                         typename cpx<R>::T& z2) {
+    using C = typename cpx<R>::T;
+    const R Lq = b.P01 + L2.x * L2.x + L2.y * L2.y;
+    if (!(Lq > (R)0)) {
+        z1 = z2 = mk((R)0, (R)0);
+        return;
+    }
+    C ed, eW, xW;
+    R een;
+    if (!alt) {
+        ed = b.S01 + L2;
+        eW = W0 + W1 + W2;
+        xW = cmul(L2 - b.L1, W0) + cmul(b.L0 - L2, W1) + cmul(b.L1 - b.L0, W2);
+        een = 3;
+    } else {
+        ed = b.D01;
+        eW = W0 - W1;
+        xW = cmul(b.S01, W2) - cmul(L2, W0 + W1);
+        een = 2;
+    }
+    const R r2 = rsq(een * Lq - (ed.x * ed.x + ed.y * ed.y));
+    const C lw = cmulc(b.L0, W0) + cmulc(b.L1, W1) + cmulc(L2, W2);     // conj(Lambda).W
+    z1 = r2 * (Lq * eW - cmul(ed, lw));
+    z2 = (root(Lq) * r2) * xW;
 }
 
 __device__ __forceinline__ void cp_async(float* dst, const float* src) {
@@ -81,7 +156,7 @@ struct ZTile {
     C tw[L];
     C tws[L][TP];
     C L2[L][TP];
-    C L0[TP], L1[TP];
+    PencilBasis<R> PB[TP];
     F F3[TP];
     uint32_t bits[L];
 };
@@ -97,8 +172,8 @@ __device__ __forceinline__ void ztile_setup(ZTile<R, L, TP>& T, const KParams<R>
     }
     for (int pp = tid; pp < TP; pp += NT) {
         const int p = min(p0 + pp, n1 - 1);
-        T.L0[pp] = lambda_of(p, n1, P.f1, P.inv_dx);
-        T.L1[pp] = lambda_of(q, n2, P.f2[p], P.inv_dy);
+        const typename cpx<R>::T L0 = lambda_of(p, n1, P.f1, P.inv_dx), L1 = lambda_of(q, n2, P.f2[p], P.inv_dy);
+        T.PB[pp] = PencilBasis<R>{L0, L1, L0 + L1, L0 - L1, L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y};
         T.F3[pp] = P.f3[(size_t)q * n1 + p];
     }
     __syncthreads();
@@ -117,7 +192,7 @@ __device__ __forceinline__ void ztile_setup(ZTile<R, L, TP>& T, const KParams<R>
 // three components; thread (pp, k1): second radix step.
 // ---------------------------------------------------------------------------
 template <typename R, int L, int TP>
-__global__ void __launch_bounds__(TP * Sp<L>::RMAX, ZOcc<L, TP * Sp<L>::RMAX>::value)
+__global__ void __launch_bounds__(TP * Sp<L>::RMAX, ZOcc<L, TP * Sp<L>::RMAX, false>::value)
 k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::T* __restrict__ W,
        int m, int vpc) {
     using C = typename cpx<R>::T;
@@ -149,15 +224,14 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
 #pragma unroll
             for (int t1 = 0; t1 < R1; ++t1) {
                 const int r = t + R2 * t1;
-                const Basis<R> b = make_basis<R>(T.L0[pp], T.L1[pp], T.L2[r][pp], (T.bits[r] >> pp) & 1u);
-                const C s1 = b.sig * a1[t1], s2 = b.sig * a2[t1];
-                x0[t1] = cmul(b.p1[0], s1) + cmul(b.p2[0], s2);
-                Y[(L + r) * TP + pp] = cmul(b.p1[1], s1) + cmul(b.p2[1], s2);
-                Y[(2 * L + r) * TP + pp] = cmul(b.p1[2], s1) + cmul(b.p2[2], s2);
+                C o1, o2;
+                expand<R>(T.PB[pp], T.L2[r][pp], (T.bits[r] >> pp) & 1u, a1[t1], a2[t1], x0[t1], o1, o2);
+                Y[(L + r) * TP + pp] = o1;
+                Y[(2 * L + r) * TP + pp] = o2;
             }
             Dft<R1, true, C>::run(x0);
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) Y[(k1 * R2 + t) * TP + pp] = twid<true>(x0[k1], T.tw, t * k1);
+            for (int k1 = 0; k1 < R1; ++k1) Y[(k1 * R2 + t) * TP + pp] = twid<true>(x0[k1], T.tw, t, k1);
 #pragma unroll
             for (int l = 1; l < 3; ++l) {
 #pragma unroll
@@ -165,7 +239,7 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
                 Dft<R1, true, C>::run(x0);
 #pragma unroll
                 for (int k1 = 0; k1 < R1; ++k1)
-                    Y[(l * L + k1 * R2 + t) * TP + pp] = twid<true>(x0[k1], T.tw, t * k1);
+                    Y[(l * L + k1 * R2 + t) * TP + pp] = twid<true>(x0[k1], T.tw, t, k1);
             }
         }
         __syncthreads();
@@ -195,7 +269,7 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
 // Z-out: conj D_a3 twist -> forward z-DFT -> Pi_r^H contraction, Sigma_r.
 // ---------------------------------------------------------------------------
 template <typename R, int L, int TP>
-__global__ void __launch_bounds__(TP * Sp<L>::RMAX, ZOcc<L, TP * Sp<L>::RMAX>::value)
+__global__ void __launch_bounds__(TP * Sp<L>::RMAX, ZOcc<L, TP * Sp<L>::RMAX, true>::value)
 k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>::T* __restrict__ out,
         int m, int vpc) {
     using C = typename cpx<R>::T;
@@ -227,7 +301,7 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
                 Dft<R1, false, C>::run(g[l]);
 #pragma unroll
                 for (int k1 = 0; k1 < R1; ++k1)
-                    Y[(l * L + k1 * R2 + t) * TP + pp] = twid<false>(g[l][k1], T.tw, t * k1);
+                    Y[(l * L + k1 * R2 + t) * TP + pp] = twid<false>(g[l][k1], T.tw, t, k1);
             }
         }
         __syncthreads();
@@ -245,12 +319,10 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
 #pragma unroll
                 for (int k2 = 0; k2 < R2; ++k2) {
                     const int r = k1 + R1 * k2;
-                    const C L2 = T.L2[r][pp];
-                    const Basis<R> b = make_basis<R>(T.L0[pp], T.L1[pp], L2, (T.bits[r] >> pp) & 1u);
-                    const C z1 = cmulc(b.p1[0], u[0][k2]) + cmulc(b.p1[1], u[1][k2]) + cmulc(b.p1[2], u[2][k2]);
-                    const C z2 = cmulc(b.p2[0], u[0][k2]) + cmulc(b.p2[1], u[1][k2]) + cmulc(b.p2[2], u[2][k2]);
-                    ov[(size_t)r * plane] = b.sig * z1;
-                    ov[n + (size_t)r * plane] = b.sig * z2;
+                    C z1, z2;
+                    contract<R>(T.PB[pp], T.L2[r][pp], (T.bits[r] >> pp) & 1u, u[0][k2], u[1][k2], u[2][k2], z1, z2);
+                    ov[(size_t)r * plane] = z1;
+                    ov[n + (size_t)r * plane] = z2;
                 }
             }
         }
@@ -330,7 +402,7 @@ k_xy3(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode, R lift_scale) 
                 const int p = w % LX, ty = w / LX;
                 Dft<RY1, true, C>::run(v[i]);
 #pragma unroll
-                for (int k1 = 0; k1 < RY1; ++k1) X[(k1 * RY2 + ty) * S + p] = twid<true>(v[i][k1], twy, ty * k1);
+                for (int k1 = 0; k1 < RY1; ++k1) X[(k1 * RY2 + ty) * S + p] = twid<true>(v[i][k1], twy, ty, k1);
             }
         }
     }
@@ -359,7 +431,7 @@ k_xy3(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode, R lift_scale) 
         for (int t1 = 0; t1 < RX1; ++t1) x[t1] = X[rho * S + tx + RX2 * t1];
         Dft<RX1, true, C>::run(x);
 #pragma unroll
-        for (int k1 = 0; k1 < RX1; ++k1) X[rho * S + tx + RX2 * k1] = twid<true>(x[k1], twx, tx * k1);
+        for (int k1 = 0; k1 < RX1; ++k1) X[rho * S + tx + RX2 * k1] = twid<true>(x[k1], twx, tx, k1);
     }
     cp_async_wait();
     __syncthreads();
@@ -375,7 +447,7 @@ k_xy3(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode, R lift_scale) 
             for (int k2 = 0; k2 < RX2; ++k2) u[k2] = (ibs[rho * S + k1 + RX1 * k2] * P.scale) * u[k2];
             Dft<RX2, false, C>::run(u);
 #pragma unroll
-            for (int k = 0; k < RX2; ++k) X[rho * S + RX2 * k1 + k] = twid<false>(u[k], twx, k1 * k);
+            for (int k = 0; k < RX2; ++k) X[rho * S + RX2 * k1 + k] = twid<false>(u[k], twx, k1, k);
         }
         __syncthreads();
         // E: forward x second step; output a = k + RX2 k2 lands in column a
@@ -402,7 +474,7 @@ k_xy3(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode, R lift_scale) 
             }
             Dft<RY2, false, C>::run(u);
 #pragma unroll
-            for (int k = 0; k < RY2; ++k) X[(k1 * RY2 + k) * S + p] = twid<false>(u[k], twy, k1 * k);
+            for (int k = 0; k < RY2; ++k) X[(k1 * RY2 + k) * S + p] = twid<false>(u[k], twy, k1, k);
         }
         __syncthreads();
         // G: forward y second step, output row k + RY2 k2 to global memory

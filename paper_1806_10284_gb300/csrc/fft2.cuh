@@ -48,10 +48,53 @@ struct Tw {
     static constexpr double s8 = 0.38268343236508977173;   // sin(pi/8)
 };
 
+// cos and sin of 2 pi j / R, evaluated at compile time: the angle is reduced by
+// exact integer arithmetic to a quarter turn q (0..3) plus y = (pi/2) r / R with
+// 0 <= y <= pi/4 (using the complementary angle above pi/4), where Taylor series
+// of 14 terms are accurate to double rounding.
+__host__ __device__ constexpr double ct_sin_q(double y) {
+    double term = y, sum = y;
+    for (int k = 1; k < 14; ++k) {
+        term *= -y * y / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ct_cos_q(double y) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 14; ++k) {
+        term *= -y * y / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+// returns cos (want_sin = false) or sin of 2 pi j / R
+__host__ __device__ constexpr double ct_trig(int j, int R, bool want_sin) {
+    constexpr double half_pi = 1.57079632679489661923132169163975;
+    const long long jj = ((long long)j % R + R) % R;
+    const long long q4 = 4 * jj;                 // angle = (pi/2) q4 / R
+    const int quad = (int)(q4 / R);
+    const long long r = q4 - (long long)quad * R;   // 0 <= r < R
+    double c = 0.0, sn = 0.0;
+    if (2 * r <= R) {
+        const double y = half_pi * (double)r / (double)R;
+        c = ct_cos_q(y);
+        sn = ct_sin_q(y);
+    } else {
+        const double y = half_pi * (double)(R - r) / (double)R;
+        c = ct_sin_q(y);
+        sn = ct_cos_q(y);
+    }
+    // rotate by quad quarter turns
+    const double cq = quad == 0 ? c : quad == 1 ? -sn : quad == 2 ? -c : sn;
+    const double sq = quad == 0 ? sn : quad == 1 ? c : quad == 2 ? -sn : -c;
+    return want_sin ? sq : cq;
+}
+
 template <int R>
-__host__ __device__ constexpr double cosr(int j);
+__host__ __device__ constexpr double cosr(int j) { return ct_trig(j, R, false); }
 template <int R>
-__host__ __device__ constexpr double sinr(int j);
+__host__ __device__ constexpr double sinr(int j) { return ct_trig(j, R, true); }
 
 template <> __host__ __device__ constexpr double cosr<6>(int j) {
     return (j % 6 == 0) ? 1.0 : (j % 6 == 1 || j % 6 == 5) ? 0.5 : (j % 6 == 3) ? -1.0 : -0.5;
