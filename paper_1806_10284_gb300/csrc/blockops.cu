@@ -432,7 +432,7 @@ __global__ void k_resid_mixed(const double2* __restrict__ X, const double2* __re
 // summed in double-float arithmetic (df64.cuh: FP64-accurate, FP32 instructions;
 // the native FP64 rate of this GPU is a small fraction of its FP32 rate), the Q
 // part (a correction orthogonal to X) in FP32.  Outputs: Xn (complex128), its
-// complex64 copy X32n, and Pn = Q M[m:] (complex64, may be null).  M column-major
+// complex64 copy X32n (may be null), and Pn = Q M[m:] (complex64, may be null).  M column-major
 // k x m, k = m + nq; its X rows are split into float pairs once per block.
 constexpr int MJ = 8;   // output columns per pass over the inputs
 
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(256) k_combine_mixed(const double2* __restrict
                 const size_t o = (size_t)jj * ld + row;
                 const float er = Er[j] + d[j].x, ei = Ei[j] + d[j].y;
                 Xn[o] = make_double2(df64::widen(Sr[j]) + df64::widen(er), df64::widen(Si[j]) + df64::widen(ei));
-                X32n[o] = make_float2(Sr[j] + er, Si[j] + ei);
+                if (X32n) X32n[o] = make_float2(Sr[j] + er, Si[j] + ei);
                 if (Pn) Pn[o] = d[j];
             }
         }
@@ -749,7 +749,7 @@ fame_status residual_mixed(fame_ctx* c, const double2* X, const double2* AX, con
 
 fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<float2>& Q, size_t ld,
                           const double2* M, double2* Xn, float2* X32n, float2* Pn, cudaStream_t st) {
-    const int nq = Q.total;
+    const int nq = Q.total;   // may be 0: Xn = X M only
     const int MP = ((m + MJ - 1) / MJ) * MJ;
     const size_t smem = (size_t)m * MP * sizeof(float4) + (size_t)nq * MP * sizeof(float2) + (size_t)nq * sizeof(void*);
     fame_status s = kernel_smem(c, (const void*)k_combine_mixed, smem);
@@ -760,7 +760,7 @@ fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<
         // adds: 15 flops counting an FMA as two), plus complex64 MACs (8 flops) for Q
         ProfScope ps(K_COMBINE_DF, true, st,
                      (double)ld * (m * sizeof(double2) + nq * sizeof(float2) +
-                                   m * (sizeof(double2) + sizeof(float2) + (Pn ? sizeof(float2) : 0))),
+                                   m * (sizeof(double2) + (X32n ? sizeof(float2) : 0) + (Pn ? sizeof(float2) : 0))),
                      (double)ld * m * (4.0 * 15.0 * m + 8.0 * nq));
         k_combine_mixed<<<152 * 8, 256, smem, st>>>(X, m, Q, ld, M, Xn, X32n, Pn);
     }

@@ -65,8 +65,8 @@ fame_status residual(fame_ctx* c, const C* X, const C* AX, const double* theta_d
 // R32 = R as complex64 (may be null)
 fame_status residual_mixed(fame_ctx* c, const double2* X, const double2* AX, const double* theta_dev,
                            int m, float2* W, float2* R32, double* part, int nblk, cudaStream_t st);
-// refinement update: Xn = X M[:m] (FP64) + Q M[m:] (FP32), X32n = complex64 copy of Xn,
-// Pn = Q M[m:] (may be null)
+// refinement update: Xn = X M[:m] (FP64 accuracy, double-float sums) + Q M[m:] (FP32),
+// X32n = complex64 copy of Xn (may be null), Pn = Q M[m:] (may be null); Q may be empty
 fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<float2>& Q, size_t ld,
                           const double2* M, double2* Xn, float2* X32n, float2* Pn, cudaStream_t st);
 // Q <- Q - X cfs (cfs m x nq), in place; FP64 arithmetic when X is complex128

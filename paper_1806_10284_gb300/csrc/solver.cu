@@ -335,7 +335,7 @@ fame_status rr64(fame_ctx* c, double2* a, double2* aa, double2* b, double2* ab, 
     fame_status s;
     if (do_apply && (s = apply_block<double2>(c, a, aa, m, st)) != FAME_OK) return s;
     const BlockList<double2> U = blocks<double2>(a, m), V = blocks<double2>(aa, m);
-    if ((s = gram<double2, double2>(c, U, concat(U, V), ld, sm.G, st)) != FAME_OK) return s;
+    if ((s = gram_herm<double2>(c, U, V, ld, sm.G, st)) != FAME_OK) return s;
     std::vector<double2> Cm;
     std::vector<double> th;
     const int got = host_rr(c, sm, m, m, 0, theta, 1e-14, th, Cm, st, &s);
@@ -343,8 +343,10 @@ fame_status rr64(fame_ctx* c, double2* a, double2* aa, double2* b, double2* ab, 
     if (got < m) return set_err(c, FAME_E_NOCONV, "refined block lost rank");
     theta = th;
     if ((s = upload_rr(c, sm, Cm, theta, st)) != FAME_OK) return s;
-    if ((s = combine<double2, double2>(c, U, ld, sm.Cd, m, m, b, nullptr, st)) != FAME_OK) return s;
-    if ((s = combine<double2, double2>(c, V, ld, sm.Cd, m, m, ab, nullptr, st)) != FAME_OK) return s;
+    // X C and (AX) C in double-float arithmetic (no complex64 part)
+    const BlockList<float2> none = blocks<float2>(nullptr, 0);
+    if ((s = combine_mixed(c, a, m, none, ld, sm.Cd, b, nullptr, nullptr, st)) != FAME_OK) return s;
+    if ((s = combine_mixed(c, aa, m, none, ld, sm.Cd, ab, nullptr, nullptr, st)) != FAME_OK) return s;
     if ((s = residual<double2>(c, b, ab, sm.theta, c->td.tinv, m, nullptr, sm.part, kResidBlocks, st)) != FAME_OK) return s;
     return read_norms(c, sm, m, theta, res, st);
 }
