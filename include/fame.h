@@ -181,6 +181,31 @@ FAME_API fame_status fame_apply_Ar_static(fame_ctx* ctx, const void* y, void* Ay
                                           void* stream);
 
 /*
+ * Apply plans -- the launch choices of fame_apply_Ar / fame_lift for one dtype
+ * (no counterpart in the paper; they change speed, not results beyond rounding).
+ *   z_kernel          : Z-in / Z-out family: 0 automatic, 1 fixed-length (complex64,
+ *                       n3 in {16,32,48,64,80,96}), 2 two-level radix, 3 Stockham.
+ *   xy_kernel         : XY family: 0 automatic, 1 fixed-length (complex64, square
+ *                       16..96 or 80x96 planes), 2 two-level plane, 3 Stockham plane,
+ *                       4 split y / x / y passes (any plane).
+ *   vectors_per_block : vectors each Z-pass thread block takes; 0 automatic.
+ * fame_set_apply_plan: FAME_E_ARG if a family is not available for the grid and
+ * dtype.  fame_autotune: times every available Z family and block size, then every
+ * XY family, on m scratch vectors (allocates 2 m 2n complex temporarily), keeps the
+ * fastest plan in the context and returns its time (ms per apply of m vectors) in
+ * *best_ms (may be NULL).  Synchronises stream.  Errors: FAME_E_ARG, FAME_E_STATE
+ * (no eps), FAME_E_NOMEM, FAME_E_CUDA.
+ */
+typedef struct fame_apply_plan {
+    int z_kernel;
+    int xy_kernel;
+    int vectors_per_block;
+} fame_apply_plan;
+FAME_API fame_status fame_set_apply_plan(fame_ctx* ctx, int dtype, const fame_apply_plan* plan);
+FAME_API fame_status fame_get_apply_plan(const fame_ctx* ctx, int dtype, fame_apply_plan* plan);
+FAME_API fame_status fame_autotune(fame_ctx* ctx, int m, int dtype, double* best_ms, void* stream);
+
+/*
  * fame_lift -- x = B^{-1} Q_r Sigma_r y, the GEP eigenvector for an A_r
  * eigenvector y (below Theorem invariant_space).
  *   y : device [m][2][n]; x : device [m][3][n] (E1, E2, E3 on the Yee grid);

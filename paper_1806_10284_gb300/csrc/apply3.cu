@@ -520,7 +520,7 @@ size_t z3_dyn_smem() { return (size_t)3 * L * kZTP * sizeof(typename cpx<R>::T);
 
 template <typename R, int L>
 fame_status launch_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
-                      typename cpx<R>::T* out, int m, bool zin, cudaStream_t st) {
+                      typename cpx<R>::T* out, int m, bool zin, int vpc_req, cudaStream_t st) {
     const int n1 = c->plan.n[0], n2 = c->plan.n[1];
     constexpr int NT = kZTP * Sp<L>::RMAX;
     const size_t smem = z3_dyn_smem<R, L>();
@@ -531,6 +531,7 @@ fame_status launch_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T
     // enough blocks for several waves over 152 SMs; the rest of the vectors loop in a block
     int vpc = 1;
     while (vpc < m && tiles * ((m + 2 * vpc - 1) / (2 * vpc)) >= 152 * 8) vpc *= 2;
+    if (vpc_req > 0) vpc = std::min(vpc_req, m);
     dim3 grid((n1 + kZTP - 1) / kZTP, n2, (m + vpc - 1) / vpc);
     const double nm = (double)c->n * m;
     ProfScope ps(zin ? K_ZIN : K_ZOUT, sizeof(R) == 8, st, 5.0 * nm * sizeof(typename cpx<R>::T),
@@ -573,14 +574,14 @@ bool xy3_supported(int n1, int n2) {
 
 template <typename R>
 fame_status run_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
-                   typename cpx<R>::T* out, int m, bool zin, cudaStream_t st) {
+                   typename cpx<R>::T* out, int m, bool zin, int vpc, cudaStream_t st) {
     switch (c->plan.n[2]) {
-        case 16: return launch_z3<R, 16>(c, P, in, out, m, zin, st);
-        case 32: return launch_z3<R, 32>(c, P, in, out, m, zin, st);
-        case 48: return launch_z3<R, 48>(c, P, in, out, m, zin, st);
-        case 64: return launch_z3<R, 64>(c, P, in, out, m, zin, st);
-        case 80: return launch_z3<R, 80>(c, P, in, out, m, zin, st);
-        case 96: return launch_z3<R, 96>(c, P, in, out, m, zin, st);
+        case 16: return launch_z3<R, 16>(c, P, in, out, m, zin, vpc, st);
+        case 32: return launch_z3<R, 32>(c, P, in, out, m, zin, vpc, st);
+        case 48: return launch_z3<R, 48>(c, P, in, out, m, zin, vpc, st);
+        case 64: return launch_z3<R, 64>(c, P, in, out, m, zin, vpc, st);
+        case 80: return launch_z3<R, 80>(c, P, in, out, m, zin, vpc, st);
+        case 96: return launch_z3<R, 96>(c, P, in, out, m, zin, vpc, st);
         default: return set_err(c, FAME_E_ARG, "fixed-length Z pass: unsupported n3");
     }
 }
@@ -603,6 +604,6 @@ fame_status run_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int
     return set_err(c, FAME_E_ARG, "fixed-length XY pass: unsupported (n1, n2)");
 }
 
-template fame_status run_z3<float>(fame_ctx*, const KParams<float>&, const float2*, float2*, int, bool,
+template fame_status run_z3<float>(fame_ctx*, const KParams<float>&, const float2*, float2*, int, bool, int,
                                    cudaStream_t);
 template fame_status run_xy3<float>(fame_ctx*, const KParams<float>&, float2*, int, int, float, cudaStream_t);

@@ -111,6 +111,13 @@ struct GrowBuf {
     size_t bytes = 0;
 };
 
+// Launch choices of the A_r apply (0 = automatic): Z-pass kernel family (1 fixed-length,
+// 2 two-level, 3 Stockham), XY kernel family (1 fixed-length, 2 two-level plane,
+// 3 Stockham plane, 4 split y / x / y passes), vectors per Z-pass block.
+struct ApplyPlan {
+    int zfam = 0, xyfam = 0, vpc = 0;
+};
+
 struct fame_ctx {
     LatticePlan plan;
     double in_vec[3][3];           // the primitive vectors as given (for kappa)
@@ -122,6 +129,7 @@ struct fame_ctx {
     bool eps_set = false;
     double mean_invB = 0.0;
     GrowBuf work;                  // transform workspace [m][3][n] complex
+    ApplyPlan apply_plan[2];       // per dtype (FAME_C64, FAME_C128), set by fame_set_apply_plan / fame_autotune
     // solver state
     std::vector<double> lambda;    // last eigenvalues
     double* Y = nullptr;           // device [nev][2][n] complex128 eigenvectors
@@ -189,12 +197,16 @@ fame_status run_grad(fame_ctx* c, const double2* Y, const double* w, int nev, do
                      cudaStream_t st);
 fame_status run_precond_table(fame_ctx* c, cudaStream_t st);
 
+// apply plans: which kernel families exist for this context's grid (transforms.cu)
+bool apply_zfam_available(const fame_ctx* c, int dtype, int zfam, int m);
+bool apply_xyfam_available(const fame_ctx* c, int dtype, int xyfam);
+
 // fixed-length passes (apply3.cu), complex64
 bool z3_supported(int L);
 bool xy3_supported(int n1, int n2);
 template <typename R>
 fame_status run_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
-                   typename cpx<R>::T* out, int m, bool zin, cudaStream_t st);
+                   typename cpx<R>::T* out, int m, bool zin, int vpc, cudaStream_t st);
 template <typename R>
 fame_status run_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int m, int mode,
                     R lift_scale, cudaStream_t st);

@@ -741,6 +741,29 @@ size_t xy2_smem(int n1, int n2) {
 // log2 of a grid length, for flop counts (5 N log2 N per complex DFT of length N)
 static double lg2(int L) { return std::log2((double)L); }
 
+bool apply_zfam_available(const fame_ctx* c, int dtype, int zfam, int m) {
+    const int n3 = c->plan.n[2];
+    switch (zfam) {
+        case 1: return dtype == FAME_C64 && z3_supported(n3);
+        case 2: return dtype == FAME_C64 ? z2_config<float>(c, m).ok : z2_config<double>(c, m).ok;
+        case 3: return true;
+        default: return false;
+    }
+}
+
+bool apply_xyfam_available(const fame_ctx* c, int dtype, int xyfam) {
+    const int n1 = c->plan.n[0], n2 = c->plan.n[1];
+    const size_t esz = dtype == FAME_C64 ? sizeof(float2) : sizeof(double2);
+    switch (xyfam) {
+        case 1: return dtype == FAME_C64 && xy3_supported(n1, n2);
+        case 2: return fft2::supported(n1) && fft2::supported(n2) &&
+                       (dtype == FAME_C64 ? xy2_smem<float>(n1, n2) : xy2_smem<double>(n1, n2)) <= kSmemCap;
+        case 3: return (size_t)(n1 + n2 + 2 * n1 * n2) * esz <= kSmemCap;
+        case 4: return true;
+        default: return false;
+    }
+}
+
 template <typename R>
 static fame_status xy_stage(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int m,
                             int mode, R lift_scale, cudaStream_t st) {
@@ -750,11 +773,15 @@ static fame_status xy_stage(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T
     const double nm = (double)c->n * m;
     const size_t plane_smem = (size_t)(n1 + n2 + 2 * n1 * n2) * sizeof(C);
     fame_status s;
+    const int dtype = dbl ? FAME_C128 : FAME_C64;
+    int fam = c->apply_plan[dtype].xyfam;
+    if (fam == 0 || !apply_xyfam_available(c, dtype, fam))
+        for (fam = 1; !apply_xyfam_available(c, dtype, fam); ++fam) {}
     if constexpr (std::is_same<R, float>::value) {
-        if (xy3_supported(n1, n2)) return run_xy3<R>(c, P, W, m, mode, lift_scale, st);
+        if (fam == 1) return run_xy3<R>(c, P, W, m, mode, lift_scale, st);
     }
     const size_t smem2 = xy2_smem<R>(n1, n2);
-    if (fft2::supported(n1) && fft2::supported(n2) && smem2 <= kSmemCap) {
+    if (fam == 2) {
         if ((s = set_smem<R>(c, (const void*)k_xy2<R>, smem2)) != FAME_OK) return s;
         const fft2::Split sx = fft2::split_of(n1), sy = fft2::split_of(n2);
         const int work = std::max(n1 * std::max(sy.R1, sy.R2), n2 * std::max(sx.R1, sx.R2));
@@ -767,7 +794,7 @@ static fame_status xy_stage(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T
         FAME_CUDA_TRY(c, cudaGetLastError());
         return FAME_OK;
     }
-    if (plane_smem <= kSmemCap) {
+    if (fam == 3) {
         if ((s = set_smem<R>(c, (const void*)k_xy<R>, plane_smem)) != FAME_OK) return s;
         const int th = (n1 * n2 >= 2048) ? 512 : 256;
         // reads and writes the 3 m n workspace once, reads B^{-1} (3n) once
@@ -821,59 +848,54 @@ fame_status run_apply(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>:
     return run_apply_into<R>(c, y, Ay, m, reinterpret_cast<C*>(c->work.p), st);
 }
 
+// One Z pass (zin: Z-in from y into the workspace; else Z-out from the workspace),
+// kernel family and vectors per block from the context's apply plan.
 template <typename R>
-fame_status run_apply_into(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* Ay, int m,
-                           typename cpx<R>::T* W, cudaStream_t st) {
+static fame_status z_pass(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
+                          typename cpx<R>::T* out, int m, bool zin, cudaStream_t st) {
     using C = typename cpx<R>::T;
-    if (m <= 0) return FAME_OK;
     const bool dbl = sizeof(R) == 8;
+    const int dtype = dbl ? FAME_C128 : FAME_C64;
     const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
     const double nm = (double)c->n * m;
+    const ApplyPlan& ap = c->apply_plan[dtype];
+    int fam = ap.zfam;
+    if (fam == 0 || !apply_zfam_available(c, dtype, fam, m))
+        for (fam = 1; !apply_zfam_available(c, dtype, fam, m); ++fam) {}
+    const int vpc_req = ap.vpc > 0 ? std::min(ap.vpc, m) : 0;
     fame_status s;
-    const KParams<R> P = make_params<R>(c);
     if constexpr (std::is_same<R, float>::value) {
-        if (z3_supported(n3)) {
-            if ((s = run_z3<R>(c, P, y, W, m, true, st)) != FAME_OK) return s;
-            if ((s = xy_stage<R>(c, P, W, m, 0, (R)0, st)) != FAME_OK) return s;
-            return run_z3<R>(c, P, W, Ay, m, false, st);
-        }
+        if (fam == 1) return run_z3<R>(c, P, in, out, m, zin, vpc_req, st);
     }
-    const Z2Cfg z2 = z2_config<R>(c, m);
-    if (z2.ok) {
-        if ((s = set_smem<R>(c, (const void*)k_zin2<R>, z2.smem)) != FAME_OK) return s;
-        if ((s = set_smem<R>(c, (const void*)k_zout2<R>, z2.smem)) != FAME_OK) return s;
+    const int kind = zin ? K_ZIN : K_ZOUT;
+    const double bytes = 5.0 * nm * sizeof(C), flops = 3 * nm * 5.0 * lg2(n3) + 60.0 * nm;
+    if (fam == 2) {
+        Z2Cfg z2 = z2_config<R>(c, m);
+        if (vpc_req) z2.vpc = vpc_req;
+        const void* fn = zin ? (const void*)k_zin2<R> : (const void*)k_zout2<R>;
+        if ((s = set_smem<R>(c, fn, z2.smem)) != FAME_OK) return s;
         const int TP = 1 << z2.lgTP;
         dim3 grid((n1 + TP - 1) / TP, n2, (m + z2.vpc - 1) / z2.vpc);
         {
-            ProfScope ps(K_ZIN, dbl, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
-            k_zin2<R><<<grid, z2.threads, z2.smem, st>>>(P, y, W, m, z2.lgTP, z2.vpc);
+            ProfScope ps(kind, dbl, st, bytes, flops);
+            if (zin)
+                k_zin2<R><<<grid, z2.threads, z2.smem, st>>>(P, in, out, m, z2.lgTP, z2.vpc);
+            else
+                k_zout2<R><<<grid, z2.threads, z2.smem, st>>>(P, in, out, m, z2.lgTP, z2.vpc);
         }
-        count_launch();
-        FAME_CUDA_TRY(c, cudaGetLastError());
-        if ((s = xy_stage<R>(c, P, W, m, 0, (R)0, st)) != FAME_OK) return s;
+    } else {
+        ZCfg z = z_config<R>(c, m);
+        if (vpc_req) z.vpc = vpc_req;
+        const void* fn = zin ? (const void*)k_zin<R> : (const void*)k_zout<R>;
+        if ((s = set_smem<R>(c, fn, z.smem)) != FAME_OK) return s;
+        dim3 grid((n1 + z.TP - 1) / z.TP, n2, (m + z.vpc - 1) / z.vpc);
         {
-            ProfScope ps(K_ZOUT, dbl, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
-            k_zout2<R><<<grid, z2.threads, z2.smem, st>>>(P, W, Ay, m, z2.lgTP, z2.vpc);
+            ProfScope ps(kind, dbl, st, bytes, flops);
+            if (zin)
+                k_zin<R><<<grid, z.threads, z.smem, st>>>(P, in, out, m, z.TP, z.vpc);
+            else
+                k_zout<R><<<grid, z.threads, z.smem, st>>>(P, in, out, m, z.TP, z.vpc);
         }
-        count_launch();
-        FAME_CUDA_TRY(c, cudaGetLastError());
-        return FAME_OK;
-    }
-    const ZCfg z = z_config<R>(c, m);
-    if ((s = set_smem<R>(c, (const void*)k_zin<R>, z.smem)) != FAME_OK) return s;
-    if ((s = set_smem<R>(c, (const void*)k_zout<R>, z.smem)) != FAME_OK) return s;
-    dim3 grid((n1 + z.TP - 1) / z.TP, n2, (m + z.vpc - 1) / z.vpc);
-    {
-        // reads y (2 m n), writes the workspace (3 m n)
-        ProfScope ps(K_ZIN, dbl, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
-        k_zin<R><<<grid, z.threads, z.smem, st>>>(P, y, W, m, z.TP, z.vpc);
-    }
-    count_launch();
-    FAME_CUDA_TRY(c, cudaGetLastError());
-    if ((s = xy_stage<R>(c, P, W, m, 0, (R)0, st)) != FAME_OK) return s;
-    {
-        ProfScope ps(K_ZOUT, dbl, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
-        k_zout<R><<<grid, z.threads, z.smem, st>>>(P, W, Ay, m, z.TP, z.vpc);
     }
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
@@ -881,43 +903,23 @@ fame_status run_apply_into(fame_ctx* c, const typename cpx<R>::T* y, typename cp
 }
 
 template <typename R>
-fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* x, int m,
-                     cudaStream_t st) {
-    using C = typename cpx<R>::T;
+fame_status run_apply_into(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* Ay, int m,
+                           typename cpx<R>::T* W, cudaStream_t st) {
     if (m <= 0) return FAME_OK;
-    const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
-    const double nm = (double)c->n * m;
     const KParams<R> P = make_params<R>(c);
     fame_status s;
-    if constexpr (std::is_same<R, float>::value) {
-        if (z3_supported(n3)) {
-            if ((s = run_z3<R>(c, P, y, x, m, true, st)) != FAME_OK) return s;
-            return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
-        }
-    }
-    const Z2Cfg z2 = z2_config<R>(c, m);
-    if (z2.ok) {
-        if ((s = set_smem<R>(c, (const void*)k_zin2<R>, z2.smem)) != FAME_OK) return s;
-        const int TP = 1 << z2.lgTP;
-        dim3 grid((n1 + TP - 1) / TP, n2, (m + z2.vpc - 1) / z2.vpc);
-        {
-            ProfScope ps(K_ZIN, sizeof(R) == 8, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
-            k_zin2<R><<<grid, z2.threads, z2.smem, st>>>(P, y, x, m, z2.lgTP, z2.vpc);
-        }
-        count_launch();
-        FAME_CUDA_TRY(c, cudaGetLastError());
-        return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
-    }
-    const ZCfg z = z_config<R>(c, m);
-    s = set_smem<R>(c, (const void*)k_zin<R>, z.smem);
-    if (s != FAME_OK) return s;
-    dim3 grid((n1 + z.TP - 1) / z.TP, n2, (m + z.vpc - 1) / z.vpc);
-    {
-        ProfScope ps(K_ZIN, sizeof(R) == 8, st, 5.0 * nm * sizeof(C), 3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
-        k_zin<R><<<grid, z.threads, z.smem, st>>>(P, y, x, m, z.TP, z.vpc);
-    }
-    count_launch();
-    FAME_CUDA_TRY(c, cudaGetLastError());
+    if ((s = z_pass<R>(c, P, y, W, m, true, st)) != FAME_OK) return s;
+    if ((s = xy_stage<R>(c, P, W, m, 0, (R)0, st)) != FAME_OK) return s;
+    return z_pass<R>(c, P, W, Ay, m, false, st);
+}
+
+template <typename R>
+fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* x, int m,
+                     cudaStream_t st) {
+    if (m <= 0) return FAME_OK;
+    const KParams<R> P = make_params<R>(c);
+    fame_status s;
+    if ((s = z_pass<R>(c, P, y, x, m, true, st)) != FAME_OK) return s;
     return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
 }
 

@@ -34,6 +34,9 @@ _SIGS = {
     "fame_apply_Ar": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "fame_apply_Ar_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "fame_lift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "fame_set_apply_plan": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "fame_get_apply_plan": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "fame_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "fame_eigs": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int, _D3, C.c_void_p,
                             C.POINTER(C.c_int), C.c_void_p]),
     "fame_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -59,6 +62,10 @@ class PlanInfo(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("perm", C.c_int * 3), ("m", C.c_int * 3), ("rho", C.c_int * 3),
                 ("s", C.c_int * 3), ("delta", C.c_double * 3), ("a", C.c_double * 9),
                 ("kappa", C.c_double * 3)]
+
+
+class ApplyPlan(C.Structure):
+    _fields_ = [("z_kernel", C.c_int), ("xy_kernel", C.c_int), ("vectors_per_block", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -250,6 +257,43 @@ class Context:
         _check(load().fame_apply_Ar_static(self._h, _ptr(y), _ptr(out), m, _dtype_code(y),
                                            _stream(stream)), self._h)
         return out
+
+    # -- apply plans and the autotuner --------------------------------------
+    def apply_plan(self, dtype=FAME_C64):
+        """{z_kernel, xy_kernel, vectors_per_block} of the apply for dtype (0 = automatic)."""
+        p = ApplyPlan()
+        _check(load().fame_get_apply_plan(self._h, int(dtype), C.byref(p)), self._h)
+        return {f: getattr(p, f) for f, _ in ApplyPlan._fields_}
+
+    def set_apply_plan(self, dtype=FAME_C64, z_kernel=0, xy_kernel=0, vectors_per_block=0):
+        p = ApplyPlan(int(z_kernel), int(xy_kernel), int(vectors_per_block))
+        _check(load().fame_set_apply_plan(self._h, int(dtype), C.byref(p)), self._h)
+
+    def autotune(self, m, dtype=FAME_C64, cache=None, stream=None):
+        """Pick the fastest apply plan for blocks of m vectors (fame_autotune).  With
+        ``cache`` (a JSON file path) a plan stored under (n1, n2, n3, precision, m) is
+        reused instead of timed, and a newly timed one is stored."""
+        import json
+        import os
+        key = "%dx%dx%d/%s/%d" % (*self.n, "c64" if int(dtype) == FAME_C64 else "c128", int(m))
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                e = table[key]
+                self.set_apply_plan(dtype, e["z_kernel"], e["xy_kernel"], e["vectors_per_block"])
+                return dict(e, cached=True)
+        ms = C.c_double(0.0)
+        _check(load().fame_autotune(self._h, int(m), int(dtype), C.byref(ms), _stream(stream)), self._h)
+        entry = dict(self.apply_plan(dtype), ms=ms.value)
+        if cache:
+            table[key] = entry
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(entry, cached=False)
 
     def lift(self, y, stream=None):
         """x = B^{-1} Q_r Sigma_r y: (m, 2n) -> (m, 3n) complex on the Yee grid."""

@@ -227,3 +227,47 @@ def test_api_errors():
     with pytest.raises(fame.FameError) as e:
         ctx.grad(1, [1.0])                               # no eigenpairs yet
     assert e.value.status == 6
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_every_apply_plan_matches_oracle(prec):
+    """Each available kernel family of the Z and XY passes, and several block sizes,
+    gives the oracle's A_r y (fame_set_apply_plan)."""
+    lat, ctx, invB, rng = _setup("sc16", (16, 16, 16), seed=2, margin=MARGIN[prec])
+    dtype = fame.FAME_C128 if prec == "c128" else fame.FAME_C64
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    m = 3
+    y = rng.standard_normal((m, 2 * lat.n)) + 1j * rng.standard_normal((m, 2 * lat.n))
+    refs = [apply_Ar(lat, y[j].reshape((2,) + lat.shape), invB).ravel() for j in range(m)]
+    yt = torch.as_tensor(y, dtype=dt, device="cuda")
+    tried = 0
+    for z in (1, 2, 3):
+        for xy in (1, 2, 3, 4):
+            for vpc in (1, 2):
+                try:
+                    ctx.set_apply_plan(dtype, z, xy, vpc)
+                except fame.FameError:
+                    continue            # family not available for this grid / precision
+                got = ctx.apply(yt).cpu().numpy()
+                for j in range(m):
+                    assert _rel(got[j], refs[j]) < (TOL64 if prec == "c128" else TOL32), (z, xy, vpc, j)
+                tried += 1
+    assert tried >= (16 if prec == "c64" else 9)
+    ctx.set_apply_plan(dtype)
+
+
+def test_autotune_and_plan_cache(tmp_path):
+    lat, ctx, invB, rng = _setup("fcc64", (32, 32, 48), seed=1)
+    cache = str(tmp_path / "plans.json")
+    first = ctx.autotune(6, fame.FAME_C64, cache=cache)
+    assert not first["cached"] and first["ms"] > 0
+    assert first["z_kernel"] in (1, 2, 3) and first["xy_kernel"] in (1, 2, 3, 4)
+    y = rng.standard_normal((2, 2 * lat.n)) + 1j * rng.standard_normal((2, 2 * lat.n))
+    got = ctx.apply(torch.as_tensor(y, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    for j in range(2):
+        assert _rel(got[j], apply_Ar(lat, y[j].reshape((2,) + lat.shape), invB).ravel()) < TOL32
+    ctx.set_apply_plan(fame.FAME_C64)
+    again = ctx.autotune(6, fame.FAME_C64, cache=cache)
+    assert again["cached"] and ctx.apply_plan(fame.FAME_C64)["z_kernel"] == first["z_kernel"]
+    with pytest.raises(fame.FameError):
+        ctx.set_apply_plan(fame.FAME_C128, z_kernel=1)       # fixed-length passes are complex64 only
