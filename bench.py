@@ -444,6 +444,8 @@ def run_ours(args, rank, world, local):
                             "solver working set > L2",
                       "parallelism": f"{world} independent k-points (one per GPU)"},
            "time_to_10_bands_s": eig_ms / args.steps / 1e3,
+           "solve_stats": {k: st[k] for k in ("iters_mixed", "iters_fp64", "applies_c64", "applies_c128",
+                                               "rr_host_ms")},
            "max_residual": resid,
            "applies_per_step": applies / max(1, world) / args.steps,
            "complex128_applies_per_step": applies64 / args.steps,

@@ -221,8 +221,10 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
 // small dense FP64 Rayleigh-Ritz (rr.cpp): solve GA c = theta GB c for the k x k
 // Hermitian pair (column-major complex, interleaved), return the nwant smallest
 // pairs.  drop: relative threshold on the scaled GB spectrum below which
-// directions are discarded.  Returns the number of pairs produced.
+// directions are discarded.  try_cholesky: reduce through the Cholesky factor of
+// GB when it is well conditioned (else, and when false, through its
+// eigen-decomposition).  Returns the number of pairs produced.
 int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double drop,
-                  double* theta, double* C);
+                  double* theta, double* C, bool try_cholesky = true);
 // Hermitian eigensolver (ascending), A column-major k x k complex; V may alias nothing.
 void herm_eig(int k, const double* A, double* w, double* V);

@@ -4,8 +4,9 @@
 // symmetric QR with the Wilkinson shift (Golub and Van Loan, Matrix
 // Computations, Sections 8.3.1-8.3.3).  The generalized pair (GA, GB) is
 // reduced to a standard problem on a GB-orthonormal basis built from the
-// eigen-decomposition of the diagonally scaled GB, dropping numerically
-// dependent directions (the SVQB step of Stathopoulos and Wu, 2002).
+// Cholesky factor of the diagonally scaled GB when it is well conditioned, else
+// from the eigen-decomposition of the scaled GB, dropping numerically dependent
+// directions (the SVQB step of Stathopoulos and Wu, 2002).
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -68,7 +69,12 @@ void tridiag_qr(int k, std::vector<double>& d, std::vector<double>& e, std::vect
 
 }  // namespace
 
-void herm_eig(int k, const double* Ain, double* w, double* Vout) {
+void herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec);
+
+void herm_eig(int k, const double* Ain, double* w, double* Vout) { herm_eig_n(k, Ain, w, Vout, k); }
+
+// as herm_eig, eigenvectors of the nvec smallest eigenvalues only (all k eigenvalues)
+void herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec) {
     std::vector<cd> A((size_t)k * k), Q((size_t)k * k, cd(0.0));
     for (size_t i = 0; i < (size_t)k * k; ++i) A[i] = cd(Ain[2 * i], Ain[2 * i + 1]);
     // Hermitise (use the lower triangle as given)
@@ -134,9 +140,9 @@ void herm_eig(int k, const double* Ain, double* w, double* Vout) {
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });
     // V = Q D Z
-    for (int jj = 0; jj < k; ++jj) {
+    for (int jj = 0; jj < k; ++jj) w[jj] = d[order[jj]];
+    for (int jj = 0; jj < nvec; ++jj) {
         const int j = order[jj];
-        w[jj] = d[j];
         for (int r = 0; r < k; ++r) {
             cd s = 0.0;
             for (int t = 0; t < k; ++t) s += at(Q, k, r, t) * ph[t] * Z[(size_t)j * k + t];
@@ -146,13 +152,92 @@ void herm_eig(int k, const double* Ain, double* w, double* Vout) {
     }
 }
 
+namespace {
+
+// Rayleigh-Ritz through the Cholesky factor of the diagonally scaled GB (unit
+// diagonal): Bs = L L^H, M = L^{-1} As L^{-H}, C = D L^{-H} Y.  Declines (returns
+// false) when a pivot falls below kMinPivot, i.e. when GB is too close to singular
+// for the factor to be trusted; the caller then takes the SVQB route.
+bool rr_cholesky(int k, const double* GA, const double* GB, const std::vector<double>& dsc, int nwant,
+                 double* theta, double* C, int* nout) {
+    constexpr double kMinPivot = 1e-4;
+    auto el = [k](const double* G, const std::vector<double>& s, int i, int j) {
+        const size_t o = 2 * ((size_t)j * k + i);
+        return cd(G[o], G[o + 1]) * (s[i] * s[j]);
+    };
+    std::vector<cd> L((size_t)k * k, cd(0.0));         // column-major lower triangle
+    for (int j = 0; j < k; ++j) {
+        double djj = el(GB, dsc, j, j).real();
+        for (int t = 0; t < j; ++t) djj -= std::norm(L[(size_t)t * k + j]);
+        if (!(djj > kMinPivot)) return false;
+        const double ljj = std::sqrt(djj);
+        L[(size_t)j * k + j] = ljj;
+        for (int i = j + 1; i < k; ++i) {
+            cd sum = el(GB, dsc, i, j);                    // lower triangle as given (i > j)
+            for (int t = 0; t < j; ++t) sum -= L[(size_t)t * k + i] * std::conj(L[(size_t)t * k + j]);
+            L[(size_t)j * k + i] = sum / ljj;
+        }
+    }
+    // X = L^{-1} As (As Hermitian from its lower triangle), column by column
+    std::vector<cd> X((size_t)k * k);
+    for (int c = 0; c < k; ++c) {
+        for (int i = 0; i < k; ++i) {
+            cd v = (i >= c) ? el(GA, dsc, i, c) : std::conj(el(GA, dsc, c, i));
+            if (i == c) v = cd(v.real(), 0.0);
+            for (int t = 0; t < i; ++t) v -= L[(size_t)t * k + i] * X[(size_t)c * k + t];
+            X[(size_t)c * k + i] = v / L[(size_t)i * k + i].real();
+        }
+    }
+    // M = X L^{-H} = (L^{-1} X^H)^H; only the lower triangle is read by herm_eig
+    std::vector<double> M(2 * (size_t)k * k, 0.0);
+    std::vector<cd> col(k);
+    for (int r = 0; r < k; ++r) {                          // column r of L^{-1} X^H
+        for (int i = 0; i < k; ++i) {
+            cd v = std::conj(X[(size_t)i * k + r]);
+            for (int t = 0; t < i; ++t) v -= L[(size_t)t * k + i] * col[t];
+            col[i] = v / L[(size_t)i * k + i].real();
+        }
+        for (int i = r; i < k; ++i) {                      // M(i, r) = conj(col[i]) ... row r of the product
+            const cd m = std::conj(col[i]);
+            M[2 * ((size_t)i * k + r)] = m.real();         // entry (r, i): upper; mirror to (i, r)
+            M[2 * ((size_t)i * k + r) + 1] = m.imag();
+            M[2 * ((size_t)r * k + i)] = m.real();
+            M[2 * ((size_t)r * k + i) + 1] = -m.imag();
+        }
+    }
+    const int nv = std::min(nwant, k);
+    std::vector<double> th(k), Y(2 * (size_t)k * k);
+    herm_eig_n(k, M.data(), th.data(), Y.data(), nv);
+    // C = D L^{-H} Y (back substitution with L^H)
+    std::vector<cd> z(k);
+    for (int j = 0; j < nv; ++j) {
+        theta[j] = th[j];
+        for (int i = k - 1; i >= 0; --i) {
+            cd v(Y[2 * ((size_t)j * k + i)], Y[2 * ((size_t)j * k + i) + 1]);
+            for (int t = i + 1; t < k; ++t) v -= std::conj(L[(size_t)i * k + t]) * z[t];
+            z[i] = v / L[(size_t)i * k + i].real();
+        }
+        for (int i = 0; i < k; ++i) {
+            const cd v = z[i] * dsc[i];
+            C[2 * ((size_t)j * k + i)] = v.real();
+            C[2 * ((size_t)j * k + i) + 1] = v.imag();
+        }
+    }
+    *nout = nv;
+    return true;
+}
+
+}  // namespace
+
 int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double drop, double* theta,
-                  double* C) {
+                  double* C, bool try_cholesky) {
     std::vector<double> dsc(k);
     for (int i = 0; i < k; ++i) {
         const double b = GB[2 * ((size_t)i * k + i)];
         dsc[i] = (b > 0.0) ? 1.0 / std::sqrt(b) : 0.0;
     }
+    int nout = 0;
+    if (try_cholesky && rr_cholesky(k, GA, GB, dsc, nwant, theta, C, &nout)) return nout;
     std::vector<double> Bs(2 * (size_t)k * k);
     for (int j = 0; j < k; ++j)
         for (int i = 0; i < k; ++i) {
@@ -193,8 +278,8 @@ int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double d
             M[2 * ((size_t)jj * kk + ii) + 1] = s.imag();
         }
     std::vector<double> th(kk), V(2 * (size_t)kk * kk);
-    herm_eig(kk, M.data(), th.data(), V.data());
-    const int nout = std::min(nwant, kk);
+    nout = std::min(nwant, kk);
+    herm_eig_n(kk, M.data(), th.data(), V.data(), nout);
     for (int j = 0; j < nout; ++j) {
         theta[j] = th[j];
         for (int i = 0; i < k; ++i) {

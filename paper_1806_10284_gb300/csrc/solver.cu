@@ -113,7 +113,8 @@ struct PhaseOut {
 // If implicit_xx > 0 the leading implicit_xx x implicit_xx blocks are replaced by
 // the identity (GB) and diag(theta_prev) (GA).
 int host_rr(fame_ctx* c, const Small& sm, int k, int m, int implicit_xx, const std::vector<double>& theta_prev,
-            double drop, std::vector<double>& theta, std::vector<double2>& Cm, cudaStream_t st, fame_status* err) {
+            double drop, std::vector<double>& theta, std::vector<double2>& Cm, cudaStream_t st, fame_status* err,
+            bool try_cholesky = true) {
     std::vector<double2> G((size_t)2 * k * k);
     cudaError_t e = cudaMemcpyAsync(G.data(), sm.G, G.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -146,7 +147,7 @@ int host_rr(fame_ctx* c, const Small& sm, int k, int m, int implicit_xx, const s
     Cm.assign((size_t)k * m, make_double2(0, 0));
     theta.assign(m, 0.0);
     const int got = rayleigh_ritz(k, GA.data(), GB.data(), m, drop, theta.data(),
-                                  reinterpret_cast<double*>(Cm.data()));
+                                  reinterpret_cast<double*>(Cm.data()), try_cholesky);
     c->stats_rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *err = FAME_OK;
     return got;
@@ -338,7 +339,8 @@ fame_status rr64(fame_ctx* c, double2* a, double2* aa, double2* b, double2* ab, 
     if ((s = gram_herm<double2>(c, U, V, ld, sm.G, st)) != FAME_OK) return s;
     std::vector<double2> Cm;
     std::vector<double> th;
-    const int got = host_rr(c, sm, m, m, 0, theta, 1e-14, th, Cm, st, &s);
+    // the final FP64 step reduces through the eigen-decomposition of X^H X
+    const int got = host_rr(c, sm, m, m, 0, theta, 1e-14, th, Cm, st, &s, false);
     if (got < 0) return s;
     if (got < m) return set_err(c, FAME_E_NOCONV, "refined block lost rank");
     theta = th;
