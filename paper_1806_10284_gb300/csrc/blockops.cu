@@ -640,8 +640,11 @@ fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, si
     const bool dbl = sizeof(CU) == 16 || sizeof(CV) == 16;
     const size_t smem = (size_t)2 * GROWS * (gram_stride(ku) * sizeof(CU) + gram_stride(kv) * sizeof(CV)) +
                         (size_t)(ku + kv) * sizeof(void*);
-    // three blocks per SM; each block's rows summed in the block's precision
-    int nblk = 152 * 3;
+    // enough blocks for about 24 resident warps per SM (small Grams have small blocks),
+    // within what shared memory allows; each block's rows summed in the block's precision
+    const int warps = threads / 32;
+    const int by_smem = std::max(1, (int)((200u * 1024u) / std::max<size_t>(smem, 1)));
+    int nblk = 152 * std::max(2, std::min({8, 24 / std::max(1, warps), by_smem}));
     size_t rpb = (ld + nblk - 1) / nblk;
     rpb = ((rpb + GROWS - 1) / GROWS) * GROWS;
     nblk = (int)((ld + rpb - 1) / rpb);
