@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--apply-plan", default=None, metavar="Z,XY,VPC",
+                    help="pin the complex64 apply plan instead of autotuning it (e.g. for profiling "
+                         "runs, where the profiler's overhead would skew the tuning)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-FP64 solve and the band-path batch after the timed steps")
     return ap.parse_args()
@@ -347,7 +350,12 @@ def run_ours(args, rank, world, local):
     dobj = np.ones(NEV)
     # the apply plan for the solver's block width, picked by timing (fame_autotune)
     m_block = NEV + max(4, (NEV + 1) // 2)
-    plan = ctx.autotune(m_block, fame.FAME_C64)
+    if args.apply_plan:
+        z, xy, vpc = (int(v) for v in args.apply_plan.split(","))
+        ctx.set_apply_plan(fame.FAME_C64, z, xy, vpc)
+        plan = dict(ctx.apply_plan(fame.FAME_C64), pinned=True)
+    else:
+        plan = ctx.autotune(m_block, fame.FAME_C64)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
