@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
     const size_t span = (size_t)TPS * CR;                         // rows per block step
     for (size_t base = blockIdx.x * span; base < ld; base += (size_t)gridDim.x * span) {
         const size_t ra = base + (size_t)(lt >> 5) * 64 + (lt & 31), rb = ra + 32;
-        const bool va = ra < ld, vb = rb < ld;
+        // rows past the end load a valid row and are never stored: unconditional loads
+        const size_t la = min(ra, ld - 1), lb = min(rb, ld - 1);
         for (int g = slot; g < ng; g += kCombineSlots) {
             C a1[CR][CJ], a2[CR][CJ];
 #pragma unroll
@@ -331,8 +332,8 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
             const C* cf = sm + g * CJ;
 #pragma unroll 4
             for (int i = 0; i < i0 && i < k; ++i) {
-                const C xa = va ? ps[i][ra] : mk((R)0, (R)0);
-                const C xb = vb ? ps[i][rb] : mk((R)0, (R)0);
+                const C xa = ps[i][la];
+                const C xb = ps[i][lb];
 #pragma unroll
                 for (int j = 0; j < CJ; ++j) {
                     const C w = cf[(size_t)i * MP + j];
@@ -342,8 +343,8 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
             }
 #pragma unroll 4
             for (int i = i0; i < k; ++i) {
-                const C xa = va ? ps[i][ra] : mk((R)0, (R)0);
-                const C xb = vb ? ps[i][rb] : mk((R)0, (R)0);
+                const C xa = ps[i][la];
+                const C xb = ps[i][lb];
 #pragma unroll
                 for (int j = 0; j < CJ; ++j) {
                     const C w = cf[(size_t)i * MP + j];
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(kCombineThreads) k_orth(const CX* __restrict__
     const size_t span = (size_t)TPS * CR;
     for (size_t base = blockIdx.x * span; base < ld; base += (size_t)gridDim.x * span) {
         const size_t ra = base + (size_t)(lt >> 5) * 64 + (lt & 31), rb = ra + 32;
-        const bool va = ra < ld, vb = rb < ld;
+        const size_t la = min(ra, ld - 1), lb = min(rb, ld - 1);   // as in k_combine
         for (int g = slot; g < ng; g += kCombineSlots) {
             // start from Q (loads in flight while the products accumulate)
             C a[CR][CJ];
@@ -546,8 +547,8 @@ __global__ void __launch_bounds__(kCombineThreads) k_orth(const CX* __restrict__
             const C* cf = sc + g * CJ;
 #pragma unroll 4
             for (int i = 0; i < m; ++i) {
-                const C xa = va ? X[(size_t)i * ld + ra] : mk((R)0, (R)0);
-                const C xb = vb ? X[(size_t)i * ld + rb] : mk((R)0, (R)0);
+                const C xa = X[(size_t)i * ld + la];
+                const C xb = X[(size_t)i * ld + lb];
 #pragma unroll
                 for (int j = 0; j < CJ; ++j) {
                     const C w = cf[(size_t)i * MP + j];
