@@ -28,6 +28,10 @@ void free_tables(fame_ctx* c) {
     free_dev(c->tf.f3); free_dev(c->td.f3);
     free_dev(c->tf.invB); free_dev(c->td.invB);
     free_dev(c->tf.tinv); free_dev(c->td.tinv);
+    free_dev(c->tf.tw3); free_dev(c->td.tw3);
+    free_dev(c->tf.lam3); free_dev(c->td.lam3);
+    free_dev(c->tf.tw2); free_dev(c->td.tw2);
+    free_dev(c->tf.tw1); free_dev(c->td.tw1);
     free_dev(c->alt_mask);
 }
 

@@ -90,6 +90,11 @@ struct KParams {
     const R* invB;                     // [3][n] 1/B
     const uint32_t* alt;               // [ceil(n/32)] reference-vector decision bits
     R scale;                           // 1/n for a full apply
+    // twist and Lambda_3 tables evaluated once per (lattice, k) in FP64
+    const typename cpx<R>::T* tw3;     // [n3][n2][n1] e^{2 pi i c f3(p, q)}, c the z index
+    const typename cpx<R>::T* lam3;    // [n3][n2][n1] Lambda_3 at frequency (p, q, r)
+    const typename cpx<R>::T* tw2;     // [n2][n1] e^{2 pi i b f2(p)}, b the y index
+    const typename cpx<R>::T* tw1;     // [n1] e^{2 pi i a f1}, a the x index
 };
 
 // Device tables of one precision.
@@ -100,6 +105,10 @@ struct DevTables {
     typename cpx<R>::T* tw[3] = {nullptr, nullptr, nullptr};
     R* invB = nullptr;
     R* tinv = nullptr;   // [n] preconditioner 1/(Lambda_q mean(1/B)), 0 where Lambda_q = 0
+    typename cpx<R>::T* tw3 = nullptr;
+    typename cpx<R>::T* lam3 = nullptr;
+    typename cpx<R>::T* tw2 = nullptr;
+    typename cpx<R>::T* tw1 = nullptr;
     typename FracT<R>::T f1;
 };
 
@@ -211,6 +220,7 @@ template <typename R>
 fame_status run_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int m, int mode,
                     R lift_scale, cudaStream_t st);
 fame_status run_basis_mask(fame_ctx* c);
+fame_status run_twist_tables(fame_ctx* c);
 
 // solver (solver.cu)
 fame_status run_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol, int max_iter,

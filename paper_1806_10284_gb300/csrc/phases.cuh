@@ -69,12 +69,23 @@ __device__ __forceinline__ bool alt_bit(const uint32_t* mask, size_t f) {
     return (mask[f >> 5] >> (f & 31)) & 1u;
 }
 
-// 1/sqrt and sqrt: the hardware approximations in single precision (a few ulp,
-// far below the complex64 path's tolerance), correctly rounded in double.
+// 1/sqrt and sqrt.  Single precision: the hardware approximation (a few ulp, far
+// below the complex64 path's tolerance).  Double precision: the single-precision
+// estimate refined by two Newton-Raphson steps y <- y (3 - x y^2) / 2 (each doubles
+// the correct digits: about 2^-22 -> 2^-44 -> below double rounding), which costs a
+// handful of FP64 operations instead of a division and a square root; arguments
+// outside the single-precision range take the division.
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double rsq(double x) {
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf((float)x);
+    const double hx = 0.5 * x;
+    y = y * (1.5 - hx * y * y);
+    y = y * (1.5 - hx * y * y);
+    return y;
+}
 __device__ __forceinline__ float root(float x) { return x * rsqrtf(x); }
-__device__ __forceinline__ double root(double x) { return sqrt(x); }
+__device__ __forceinline__ double root(double x) { return x * rsq(x); }
 
 template <typename R>
 struct Basis {

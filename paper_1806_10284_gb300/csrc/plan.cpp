@@ -208,7 +208,8 @@ fame_status build_tables(fame_ctx* c) {
     if ((st = upload(c, &c->tf.f2, f2f)) != FAME_OK) return st;
     if ((st = upload(c, &c->td.f3, f3d)) != FAME_OK) return st;
     if ((st = upload(c, &c->tf.f3, f3f)) != FAME_OK) return st;
-    return run_basis_mask(c);
+    if ((st = run_basis_mask(c)) != FAME_OK) return st;
+    return run_twist_tables(c);
 }
 
 template <typename R>
@@ -230,6 +231,10 @@ static void fill_common(const fame_ctx* c, KParams<R>& k, const DevTables<R>& t)
     }
     k.invB = t.invB;
     k.alt = c->alt_mask;
+    k.tw3 = t.tw3;
+    k.lam3 = t.lam3;
+    k.tw2 = t.tw2;
+    k.tw1 = t.tw1;
     k.scale = (R)(1.0 / (double)c->n);
 }
 

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(512) k_zin(KParams<R> P, const typename cpx<R>
             if (p < n1) {
                 const size_t f = ((size_t)r * n2 + q) * n1 + p;
                 const C y1 = yv[f], y2 = yv[n + f];
-                const C L2 = lambda_of(r, n3, P.f3[(size_t)q * n1 + p], P.inv_dz);
+                const C L2 = P.lam3[f];
                 const Basis<R> b = make_basis<R>(L0s[pp], L1s[pp], L2, alt_bit(P.alt, f));
                 const C s1 = b.sig * y1, s2 = b.sig * y2;
                 o0 = cmul(b.p1[0], s1) + cmul(b.p2[0], s2);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(512) k_zin(KParams<R> P, const typename cpx<R>
             const int l = e / tile, rem = e - l * tile, c = rem / TP, pp = rem - c * TP;
             const int p = p0 + pp;
             if (p < n1) {
-                const C x = cmul(res[e], cis(frac_mul(c, P.f3[(size_t)q * n1 + p])));
+                const C x = cmul(res[e], P.tw3[((size_t)c * n2 + q) * n1 + p]);
                 Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p] = x;
             }
         }
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(512) k_zout(KParams<R> P, const typename cpx<R
             C x = mk((R)0, (R)0);
             if (p < n1) {
                 x = Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p];
-                x = cmulc(cis(frac_mul(c, P.f3[(size_t)q * n1 + p])), x);
+                x = cmulc(P.tw3[((size_t)c * n2 + q) * n1 + p], x);
             }
             buf[e] = x;
         }
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(512) k_zout(KParams<R> P, const typename cpx<R
             const int r = e / TP, pp = e - r * TP, p = p0 + pp;
             if (p < n1) {
                 const size_t f = ((size_t)r * n2 + q) * n1 + p;
-                const C L2 = lambda_of(r, n3, P.f3[(size_t)q * n1 + p], P.inv_dz);
+                const C L2 = P.lam3[f];
                 const Basis<R> b = make_basis<R>(L0s[pp], L1s[pp], L2, alt_bit(P.alt, f));
                 const C w0 = res[e], w1 = res[tile + e], w2 = res[2 * tile + e];
                 const C z1 = cmulc(b.p1[0], w0) + cmulc(b.p1[1], w1) + cmulc(b.p1[2], w2);
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(512) k_xy(KParams<R> P, typename cpx<R>::T* __
     C* oth = (cur == A) ? B : A;
     for (int e = threadIdx.x; e < np; e += blockDim.x) {
         const int b = e / n1, p = e - b * n1;
-        cur[e] = cmul(cur[e], cis(frac_mul(b, P.f2[p])));
+        cur[e] = cmul(cur[e], P.tw2[e]);
     }
     __syncthreads();
     cur = fft_axis(cur, oth, rows, P.ax[0], twx, true);
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(512) k_xy(KParams<R> P, typename cpx<R>::T* __
         oth = (cur == A) ? B : A;
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int b = e / n1, p = e - b * n1;
-            cur[e] = cmulc(cis(frac_mul(b, P.f2[p])), cur[e]);
+            cur[e] = cmulc(P.tw2[e], cur[e]);
         }
         __syncthreads();
         cur = fft_axis(cur, oth, cols, P.ax[1], twy, false);
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(512) k_xy(KParams<R> P, typename cpx<R>::T* __
     } else {
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int a = e % n1;
-            g[e] = (ib[e] * lift_scale) * cmul(cur[e], cis(frac_mul(a, P.f1)));
+            g[e] = (ib[e] * lift_scale) * cmul(cur[e], P.tw1[a]);
         }
     }
 }
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256) k_ypass(KParams<R> P, typename cpx<R>::T*
         C x = mk((R)0, (R)0);
         if (p < n1) {
             x = g[(size_t)b * n1 + p];
-            if (dir == 1) x = cmulc(cis(frac_mul(b, P.f2[p])), x);
+            if (dir == 1) x = cmulc(P.tw2[(size_t)b * n1 + p], x);
         }
         buf[e] = x;
     }
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(256) k_ypass(KParams<R> P, typename cpx<R>::T*
         const int b = e / TP, pp = e - b * TP, p = p0 + pp;
         if (p < n1) {
             C x = res[e];
-            if (dir == 0) x = cmul(x, cis(frac_mul(b, P.f2[p])));
+            if (dir == 0) x = cmul(x, P.tw2[(size_t)b * n1 + p]);
             g[(size_t)b * n1 + p] = x;
         }
     }
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(256) k_xpass(KParams<R> P, typename cpx<R>::T*
         const int l = (int)((row / ((long long)n3 * n2)) % 3);
         const R ib = P.invB[(size_t)l * nsp + (size_t)rb * n1 + a];
         if (mode == 0) cur[e] = (ib * P.scale) * cur[e];
-        else cur[e] = (ib * lift_scale) * cmul(cur[e], cis(frac_mul(a, P.f1)));
+        else cur[e] = (ib * lift_scale) * cmul(cur[e], P.tw1[a]);
     }
     __syncthreads();
     if (mode == 0) cur = fft_axis(cur, oth, rows, P.ax[0], tw, false);
@@ -461,6 +461,41 @@ __global__ void k_basis_mask(KParams<double> P, uint32_t* __restrict__ mask) {
             if (Lq > 0.0 && g1 < kGTol * 3.0 * Lq) bits |= 1u << b;
         }
         mask[wd] = bits;
+    }
+}
+
+// Twist and Lambda_3 tables of one (lattice, k): D_a3 twist e^{2 pi i c f3(p,q)} and
+// Lambda_3 at every (p, q, c/r) in [n3][n2][n1] order, D_a2 twist e^{2 pi i b f2(p)}
+// in [n2][n1], D_a1 twist e^{2 pi i a f1} in [n1]; evaluated in FP64, stored in
+// both precisions.
+__global__ void k_twist_tables(KParams<double> P, float2* __restrict__ tw3f, double2* __restrict__ tw3d,
+                               float2* __restrict__ lam3f, double2* __restrict__ lam3d,
+                               float2* __restrict__ tw2f, double2* __restrict__ tw2d,
+                               float2* __restrict__ tw1f, double2* __restrict__ tw1d) {
+    const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
+    const size_t plane = (size_t)n1 * n2, n = plane * n3;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t f = blockIdx.x * (size_t)blockDim.x + threadIdx.x; f < n; f += stride) {
+        const size_t pq = f % plane;
+        const int c = (int)(f / plane);
+        const double F3 = P.f3[pq];
+        const double2 t = cis(frac_mul(c, F3));
+        const double2 l = lambda_of(c, n3, F3, P.inv_dz);
+        tw3d[f] = t;
+        tw3f[f] = make_float2((float)t.x, (float)t.y);
+        lam3d[f] = l;
+        lam3f[f] = make_float2((float)l.x, (float)l.y);
+    }
+    for (size_t f = blockIdx.x * (size_t)blockDim.x + threadIdx.x; f < plane; f += stride) {
+        const int p = (int)(f % n1), b = (int)(f / n1);
+        const double2 t = cis(frac_mul(b, P.f2[p]));
+        tw2d[f] = t;
+        tw2f[f] = make_float2((float)t.x, (float)t.y);
+    }
+    for (size_t a = blockIdx.x * (size_t)blockDim.x + threadIdx.x; a < (size_t)n1; a += stride) {
+        const double2 t = cis(frac_mul((int)a, P.f1));
+        tw1d[a] = t;
+        tw1f[a] = make_float2((float)t.x, (float)t.y);
     }
 }
 
@@ -526,7 +561,7 @@ __global__ void __launch_bounds__(512) k_zin2(KParams<R> P, const typename cpx<R
             if (p < n1) {
                 const size_t f = ((size_t)r * n2 + q) * n1 + p;
                 const C y1 = yv[f], y2 = yv[n + f];
-                const C L2 = lambda_of(r, n3, F3s[pp], P.inv_dz);
+                const C L2 = P.lam3[f];
                 const Basis<R> b = make_basis<R>(L0s[pp], L1s[pp], L2, alt_bit(P.alt, f));
                 const C s1 = b.sig * y1, s2 = b.sig * y2;
                 o0 = cmul(b.p1[0], s1) + cmul(b.p2[0], s2);
@@ -544,7 +579,7 @@ __global__ void __launch_bounds__(512) k_zin2(KParams<R> P, const typename cpx<R
             [&](int pc, int c, C val) {
                 const int l = pc >> lgTP, pp = pc & (TP - 1), p = p0 + pp;
                 if (p < n1)
-                    Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p] = cmul(val, cis(frac_mul(c, F3s[pp])));
+                    Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p] = cmul(val, P.tw3[((size_t)c * n2 + q) * n1 + p]);
             });
     }
 }
@@ -584,7 +619,7 @@ __global__ void __launch_bounds__(512) k_zout2(KParams<R> P, const typename cpx<
                 const int l = pc >> lgTP, pp = pc & (TP - 1), p = p0 + pp;
                 if (p >= n1) return mk((R)0, (R)0);
                 const C x = Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p];
-                return cmulc(cis(frac_mul(c, F3s[pp])), x);
+                return cmulc(P.tw3[((size_t)c * n2 + q) * n1 + p], x);
             },
             [&](int pc, int r, C val) { X[r * NP + pc] = val; });
         C* ov = out + (size_t)v * 2 * n;
@@ -592,7 +627,7 @@ __global__ void __launch_bounds__(512) k_zout2(KParams<R> P, const typename cpx<
             const int r = e >> lgTP, pp = e & (TP - 1), p = p0 + pp;
             if (p < n1) {
                 const size_t f = ((size_t)r * n2 + q) * n1 + p;
-                const C L2 = lambda_of(r, n3, F3s[pp], P.inv_dz);
+                const C L2 = P.lam3[f];
                 const Basis<R> b = make_basis<R>(L0s[pp], L1s[pp], L2, alt_bit(P.alt, f));
                 const C w0 = X[r * NP + pp], w1 = X[r * NP + TP + pp], w2 = X[r * NP + 2 * TP + pp];
                 const C z1 = cmulc(b.p1[0], w0) + cmulc(b.p1[1], w1) + cmulc(b.p1[2], w2);
@@ -635,7 +670,7 @@ __global__ void __launch_bounds__(512) k_xy2(KParams<R> P, typename cpx<R>::T* _
     // inverse y-DFT over columns, then D_a2
     fft2::pencils_any<true>(
         n2, n1, twy, Y, [&](int p, int b) { return X[b * S + p]; },
-        [&](int p, int b, C v) { X[b * S + p] = cmul(v, cis(frac_mul(b, F2s[p]))); });
+        [&](int p, int b, C v) { X[b * S + p] = cmul(v, P.tw2[b * n1 + p]); });
     // inverse x-DFT over rows
     fft2::pencils_any<true>(
         n1, n2, twx, Y, [&](int b, int a) { return X[b * S + a]; },
@@ -652,7 +687,7 @@ __global__ void __launch_bounds__(512) k_xy2(KParams<R> P, typename cpx<R>::T* _
             [&](int b, int a, C v) { X[b * S + a] = v; });
         fft2::pencils_any<false>(
             n2, n1, twy, Y,
-            [&](int p, int b) { return cmulc(cis(frac_mul(b, F2s[p])), X[b * S + p]); },
+            [&](int p, int b) { return cmulc(P.tw2[b * n1 + p], X[b * S + p]); },
             [&](int p, int b, C v) { X[b * S + p] = v; });
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int b = fdiv(e, inv_n1), a = e - b * n1;
@@ -661,7 +696,7 @@ __global__ void __launch_bounds__(512) k_xy2(KParams<R> P, typename cpx<R>::T* _
     } else {
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int b = fdiv(e, inv_n1), a = e - b * n1;
-            g[e] = (ib[e] * lift_scale) * cmul(X[b * S + a], cis(frac_mul(a, P.f1)));
+            g[e] = (ib[e] * lift_scale) * cmul(X[b * S + a], P.tw1[a]);
         }
     }
 }
@@ -960,6 +995,27 @@ fame_status run_basis_mask(fame_ctx* c) {
     }
     const KParams<double> Pd = make_params<double>(c);
     k_basis_mask<<<608, 128>>>(Pd, c->alt_mask);
+    count_launch();
+    FAME_CUDA_TRY(c, cudaGetLastError());
+    FAME_CUDA_TRY(c, cudaDeviceSynchronize());
+    return FAME_OK;
+}
+
+fame_status run_twist_tables(fame_ctx* c) {
+    const size_t n = (size_t)c->n, plane = (size_t)c->plan.n[0] * c->plan.n[1], n1 = (size_t)c->plan.n[0];
+    struct { void** p; size_t bytes; } bufs[] = {
+        {(void**)&c->tf.tw3, n * sizeof(float2)},   {(void**)&c->td.tw3, n * sizeof(double2)},
+        {(void**)&c->tf.lam3, n * sizeof(float2)},  {(void**)&c->td.lam3, n * sizeof(double2)},
+        {(void**)&c->tf.tw2, plane * sizeof(float2)}, {(void**)&c->td.tw2, plane * sizeof(double2)},
+        {(void**)&c->tf.tw1, n1 * sizeof(float2)},  {(void**)&c->td.tw1, n1 * sizeof(double2)}};
+    for (auto& b : bufs)
+        if (!*b.p && cudaMalloc(b.p, b.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, FAME_E_NOMEM, "cudaMalloc twist tables");
+        }
+    const KParams<double> Pd = make_params<double>(c);
+    k_twist_tables<<<1216, 256>>>(Pd, c->tf.tw3, c->td.tw3, c->tf.lam3, c->td.lam3, c->tf.tw2, c->td.tw2,
+                                  c->tf.tw1, c->td.tw1);
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
     FAME_CUDA_TRY(c, cudaDeviceSynchronize());
