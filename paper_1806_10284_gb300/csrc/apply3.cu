@@ -54,79 +54,6 @@ __device__ __forceinline__ C twid(C x, const C* tw, int t, int k) {
     return cmul(x, w);
 }
 
-// Per-pencil parts of the range basis (one x-frequency p at one y-frequency q):
-// Lambda_1, Lambda_2, |Lambda_1|^2 + |Lambda_2|^2, and the partial sums
-// Lambda_1 + Lambda_2, Lambda_1 - Lambda_2 of e.Lambda for the two reference
-// vectors e = (1,1,1) and e = (1,-1,0).
-template <typename R>
-struct PencilBasis {
-    typename cpx<R>::T L0, L1, S01, D01;
-    R P01;
-};
-
-// (o_0, o_1, o_2) = Sigma_r [Pi_1 Pi_2] (y1, y2) at one frequency, eqs. (range_basis1),
-// (range_basis2), (SVD) written out: with g = |e|^2 Lq - |e.Lambda|^2 and x = e x Lambda,
-//   o_l = g^{-1/2} [ (Lq e_l - Lambda_l conj(e.Lambda)) y1 + Lq^{1/2} conj(x_l) y2 ].
-template <typename R>
-__device__ __forceinline__ void expand(const PencilBasis<R>& b, typename cpx<R>::T L2, bool alt,
-                                       typename cpx<R>::T y1, typename cpx<R>::T y2,
-                                       typename cpx<R>::T& o0, typename cpx<R>::T& o1,
-                                       typename cpx<R>::T& o2) {
-    using C = typename cpx<R>::T;
-    const R Lq = b.P01 + L2.x * L2.x + L2.y * L2.y;
-    if (!(Lq > (R)0)) {
-        o0 = o1 = o2 = mk((R)0, (R)0);
-        return;
-    }
-    C ed, x0, x1, x2;
-    R een, e1, e2;
-    if (!alt) {
-        ed = b.S01 + L2; x0 = L2 - b.L1; x1 = b.L0 - L2; x2 = b.L1 - b.L0; een = 3; e1 = 1; e2 = 1;
-    } else {
-        ed = b.D01; x0 = mk(-L2.x, -L2.y); x1 = x0; x2 = b.S01; een = 2; e1 = -1; e2 = 0;
-    }
-    const R r2 = rsq(een * Lq - (ed.x * ed.x + ed.y * ed.y));
-    const R sr = root(Lq) * r2;
-    const C u = r2 * y1, v = sr * y2;
-    const C d = cmulc(ed, u);                        // conj(e.Lambda) u
-    const C w = Lq * u;
-    o0 = w - cmul(b.L0, d) + cmulc(x0, v);
-    o1 = e1 * w - cmul(b.L1, d) + cmulc(x1, v);
-    o2 = e2 * w - cmul(L2, d) + cmulc(x2, v);
-}
-
-// The adjoint: (z1, z2) = Sigma_r [Pi_1 Pi_2]^H (W_0, W_1, W_2) at one frequency,
-//   z1 = g^{-1/2} [ Lq e.W - (e.Lambda) conj(Lambda).W ],  z2 = g^{-1/2} Lq^{1/2} x.W.
-template <typename R>
-__device__ __forceinline__ void contract(const PencilBasis<R>& b, typename cpx<R>::T L2, bool alt,
-                                         typename cpx<R>::T W0, typename cpx<R>::T W1,
-                                         typename cpx<R>::T W2, typename cpx<R>::T& z1,
-                                         typename cpx<R>::T& z2) {
-    using C = typename cpx<R>::T;
-    const R Lq = b.P01 + L2.x * L2.x + L2.y * L2.y;
-    if (!(Lq > (R)0)) {
-        z1 = z2 = mk((R)0, (R)0);
-        return;
-    }
-    C ed, eW, xW;
-    R een;
-    if (!alt) {
-        ed = b.S01 + L2;
-        eW = W0 + W1 + W2;
-        xW = cmul(L2 - b.L1, W0) + cmul(b.L0 - L2, W1) + cmul(b.L1 - b.L0, W2);
-        een = 3;
-    } else {
-        ed = b.D01;
-        eW = W0 - W1;
-        xW = cmul(b.S01, W2) - cmul(L2, W0 + W1);
-        een = 2;
-    }
-    const R r2 = rsq(een * Lq - (ed.x * ed.x + ed.y * ed.y));
-    const C lw = cmulc(b.L0, W0) + cmulc(b.L1, W1) + cmulc(L2, W2);     // conj(Lambda).W
-    z1 = r2 * (Lq * eW - cmul(ed, lw));
-    z2 = (root(Lq) * r2) * xW;
-}
-
 __device__ __forceinline__ void cp_async(float* dst, const float* src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");

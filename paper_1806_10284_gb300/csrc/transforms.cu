@@ -561,12 +561,10 @@ __global__ void __launch_bounds__(512) k_zin2(KParams<R> P, const typename cpx<R
             if (p < n1) {
                 const size_t f = ((size_t)r * n2 + q) * n1 + p;
                 const C y1 = yv[f], y2 = yv[n + f];
-                const C L2 = P.lam3[f];
-                const Basis<R> b = make_basis<R>(L0s[pp], L1s[pp], L2, alt_bit(P.alt, f));
-                const C s1 = b.sig * y1, s2 = b.sig * y2;
-                o0 = cmul(b.p1[0], s1) + cmul(b.p2[0], s2);
-                o1 = cmul(b.p1[1], s1) + cmul(b.p2[1], s2);
-                o2 = cmul(b.p1[2], s1) + cmul(b.p2[2], s2);
+                const C L0 = L0s[pp], L1 = L1s[pp];
+                const PencilBasis<R> pb{L0, L1, L0 + L1, L0 - L1,
+                                        L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y};
+                expand<R>(pb, P.lam3[f], alt_bit(P.alt, f), y1, y2, o0, o1, o2);
             }
             X[r * NP + pp] = o0;
             X[r * NP + TP + pp] = o1;
@@ -627,13 +625,14 @@ __global__ void __launch_bounds__(512) k_zout2(KParams<R> P, const typename cpx<
             const int r = e >> lgTP, pp = e & (TP - 1), p = p0 + pp;
             if (p < n1) {
                 const size_t f = ((size_t)r * n2 + q) * n1 + p;
-                const C L2 = P.lam3[f];
-                const Basis<R> b = make_basis<R>(L0s[pp], L1s[pp], L2, alt_bit(P.alt, f));
-                const C w0 = X[r * NP + pp], w1 = X[r * NP + TP + pp], w2 = X[r * NP + 2 * TP + pp];
-                const C z1 = cmulc(b.p1[0], w0) + cmulc(b.p1[1], w1) + cmulc(b.p1[2], w2);
-                const C z2 = cmulc(b.p2[0], w0) + cmulc(b.p2[1], w1) + cmulc(b.p2[2], w2);
-                ov[f] = b.sig * z1;
-                ov[n + f] = b.sig * z2;
+                const C L0 = L0s[pp], L1 = L1s[pp];
+                const PencilBasis<R> pb{L0, L1, L0 + L1, L0 - L1,
+                                        L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y};
+                C z1, z2;
+                contract<R>(pb, P.lam3[f], alt_bit(P.alt, f), X[r * NP + pp], X[r * NP + TP + pp],
+                            X[r * NP + 2 * TP + pp], z1, z2);
+                ov[f] = z1;
+                ov[n + f] = z2;
             }
         }
         __syncthreads();
