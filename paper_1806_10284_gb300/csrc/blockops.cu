@@ -380,15 +380,16 @@ __global__ void k_resid(const C* __restrict__ X, const C* __restrict__ AX,
     const int j = blockIdx.y;
     const size_t ld = 2 * n;
     const R th = (R)theta[j];
-    double s = 0.0;
+    R sr = 0;                       // a thread's few rows summed in the block's precision
     for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < ld;
          row += (size_t)gridDim.x * blockDim.x) {
         const C x = X[(size_t)j * ld + row], ax = AX[(size_t)j * ld + row];
         const C r = mk(ax.x - th * x.x, ax.y - th * x.y);
-        s += (double)r.x * r.x + (double)r.y * r.y;
+        sr += r.x * r.x + r.y * r.y;
         const R t = tinv[row < n ? row : row - n];
         if (W) W[(size_t)j * ld + row] = mk(t * r.x, t * r.y);
     }
+    double s = (double)sr;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -409,16 +410,17 @@ __global__ void k_resid_mixed(const double2* __restrict__ X, const double2* __re
     const int j = blockIdx.y;
     const size_t ld = 2 * n;
     const double th = theta[j];
-    double s = 0.0;
+    float sf = 0.0f;                // |R|^2 of a thread's few rows from R rounded to float
     for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < ld;
          row += (size_t)gridDim.x * blockDim.x) {
         const double2 x = X[(size_t)j * ld + row], ax = AX[(size_t)j * ld + row];
-        const double rx = ax.x - th * x.x, ry = ax.y - th * x.y;
-        s += rx * rx + ry * ry;
+        const float rx = df64::narrow(ax.x - th * x.x), ry = df64::narrow(ax.y - th * x.y);
+        sf += rx * rx + ry * ry;
         const float t = tinv[row < n ? row : row - n];
-        W[(size_t)j * ld + row] = make_float2(t * (float)rx, t * (float)ry);
-        if (R32) R32[(size_t)j * ld + row] = make_float2((float)rx, (float)ry);
+        W[(size_t)j * ld + row] = make_float2(t * rx, t * ry);
+        if (R32) R32[(size_t)j * ld + row] = make_float2(rx, ry);
     }
+    double s = (double)sf;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();

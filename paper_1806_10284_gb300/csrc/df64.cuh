@@ -40,6 +40,12 @@ __device__ __forceinline__ Split split(double x) {
     return r;
 }
 
+// x rounded to a float (h + l in one single-precision add), without an FP64 conversion
+__device__ __forceinline__ float narrow(double x) {
+    const Split s = split(x);
+    return s.h + s.l;
+}
+
 // exact float -> double
 __device__ __forceinline__ double widen(float f) {
     const unsigned u = __float_as_uint(f);
