@@ -184,10 +184,13 @@ FAME_API fame_status fame_apply_Ar_static(fame_ctx* ctx, const void* y, void* Ay
  * Apply plans -- the launch choices of fame_apply_Ar / fame_lift for one dtype
  * (no counterpart in the paper; they change speed, not results beyond rounding).
  *   z_kernel          : Z-in / Z-out family: 0 automatic, 1 fixed-length (complex64,
- *                       n3 in {16,32,48,64,80,96}), 2 two-level radix, 3 Stockham.
+ *                       n3 in {16,32,48,64,80,96}; each block issues the loads of its
+ *                       next vector while it transforms the current one), 2 two-level
+ *                       radix, 3 Stockham, 4 fixed-length without that prefetch.
  *   xy_kernel         : XY family: 0 automatic, 1 fixed-length (complex64, square
  *                       16..96 or 80x96 planes), 2 two-level plane, 3 Stockham plane,
- *                       4 split y / x / y passes (any plane).
+ *                       4 split y / x / y passes (any plane), 5 fixed-length with 512
+ *                       threads per plane (complex64, 64x64, 96x96, 80x96).
  *   vectors_per_block : vectors each Z-pass thread block takes; 0 automatic.
  * fame_set_apply_plan: FAME_E_ARG if a family is not available for the grid and
  * dtype.  fame_autotune: times every available Z family and block size, then every

@@ -11,11 +11,15 @@
 //    global memory (Z passes: the frequency expansion Sigma_r Pi_r is applied
 //    on the fly) and the last radix step writes straight to global memory
 //    (Z-in: with the D_a3 twist; Z-out: with the Pi_r^H contraction), so a Z
-//    pass does a single shared-memory exchange per vector;
+//    pass does a single shared-memory exchange per vector; a Z block that takes
+//    several vectors can request the next vector's inputs into registers while
+//    it transforms the current one, so its loads overlap its arithmetic;
 //  * in the XY pass every radix step writes its outputs to the slots it read
 //    its inputs from, so one plane buffer serves all seven steps with one
 //    barrier between steps; the B^{-1} plane is copied to shared memory
-//    asynchronously (cp.async) while the y and x inverse transforms run.
+//    asynchronously (cp.async) while the y and x inverse transforms run.  The
+//    plane is taken by 256 threads, or for the larger planes by 512 threads
+//    with a register budget of three blocks per SM.
 //
 // Radix steps follow the four-step split of fft2.cuh: for L = A * B and input
 // index t + B t1 (t < B, t1 < A), an A-point DFT over t1, the twiddle
@@ -37,9 +41,10 @@ template <int L> struct Sp {
     static constexpr int RMAX = R1 > R2 ? R1 : R2;
 };
 // Z-pass blocks per SM asked of the register allocator: about 640 resident threads
-// where that fits without spills, else about 512
-template <int L, int NT, bool OUT> struct ZOcc {
-    static constexpr int threads = ((L == 64 && !OUT) || L <= 32) ? 640 : 512;
+// where that fits without spills, else about 512 (the prefetching Z-in holds a second
+// vector's inputs in registers)
+template <int L, int NT, bool OUT, bool PF = false> struct ZOcc {
+    static constexpr int threads = ((L == 64 && !OUT && !PF) || L <= 32) ? 640 : 512;
     static constexpr int value = threads / NT > 0 ? threads / NT : 1;
 };
 
@@ -118,8 +123,8 @@ __device__ __forceinline__ void ztile_setup(ZTile<R, L, TP>& T, const KParams<R>
 // [z vpc, (z+1) vpc).  Thread (pp, t): first radix step of pencil pp for the
 // three components; thread (pp, k1): second radix step.
 // ---------------------------------------------------------------------------
-template <typename R, int L, int TP>
-__global__ void __launch_bounds__(TP * Sp<L>::RMAX, ZOcc<L, TP * Sp<L>::RMAX, false>::value)
+template <typename R, int L, int TP, bool PF>
+__global__ void __launch_bounds__(TP * Sp<L>::RMAX, (ZOcc<L, TP * Sp<L>::RMAX, false, PF>::value))
 k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::T* __restrict__ W,
        int m, int vpc) {
     using C = typename cpx<R>::T;
@@ -135,16 +140,22 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
     const bool valid = p < n1;
     const size_t base = (size_t)q * n1 + p;
     const int v1 = min(m, (int)(blockIdx.z + 1) * vpc);
+    // this thread's inputs of vector v (rows t + R2 t1 of pencil pp, both components);
+    // with PF the next vector's are requested as soon as these are consumed
+    C a1[R1], a2[R1];
+    auto load = [&](int v) {
+        const C* yv = y + (size_t)v * 2 * n + base;
+#pragma unroll
+        for (int t1 = 0; t1 < R1; ++t1) {
+            const size_t off = (size_t)(t + R2 * t1) * plane;
+            a1[t1] = valid ? yv[off] : mk((R)0, (R)0);
+            a2[t1] = valid ? yv[n + off] : mk((R)0, (R)0);
+        }
+    };
+    if (PF && t < R2 && blockIdx.z * vpc < v1) load(blockIdx.z * vpc);
     for (int v = blockIdx.z * vpc; v < v1; ++v) {
         if (t < R2) {
-            const C* yv = y + (size_t)v * 2 * n + base;
-            C a1[R1], a2[R1];
-#pragma unroll
-            for (int t1 = 0; t1 < R1; ++t1) {
-                const size_t off = (size_t)(t + R2 * t1) * plane;
-                a1[t1] = valid ? yv[off] : mk((R)0, (R)0);
-                a2[t1] = valid ? yv[n + off] : mk((R)0, (R)0);
-            }
+            if (!PF) load(v);
             // expansion; components 1 and 2 wait in this thread's own slots of Y
             // (rows t + R2 j of pencil pp), which its radix step overwrites in turn
             C x0[R1];
@@ -156,6 +167,7 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
                 Y[(L + r) * TP + pp] = o1;
                 Y[(2 * L + r) * TP + pp] = o2;
             }
+            if (PF && v + 1 < v1) load(v + 1);
             Dft<R1, true, C>::run(x0);
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1) Y[(k1 * R2 + t) * TP + pp] = twid<true>(x0[k1], T.tw, t, k1);
@@ -195,7 +207,7 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
 // ---------------------------------------------------------------------------
 // Z-out: conj D_a3 twist -> forward z-DFT -> Pi_r^H contraction, Sigma_r.
 // ---------------------------------------------------------------------------
-template <typename R, int L, int TP>
+template <typename R, int L, int TP, bool PF>
 __global__ void __launch_bounds__(TP * Sp<L>::RMAX, ZOcc<L, TP * Sp<L>::RMAX, true>::value)
 k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>::T* __restrict__ out,
         int m, int vpc) {
@@ -212,15 +224,21 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
     const bool valid = p < n1;
     const size_t base = (size_t)q * n1 + p;
     const int v1 = min(m, (int)(blockIdx.z + 1) * vpc);
+    // this thread's inputs of vector v; with PF the next vector's are requested
+    // once these have gone through the first radix step
+    C g[3][R1];
+    auto load = [&](int v) {
+        const C* Wv = W + (size_t)v * 3 * n + base;
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int t1 = 0; t1 < R1; ++t1)
+                g[l][t1] = valid ? Wv[(size_t)l * n + (size_t)(t + R2 * t1) * plane] : mk((R)0, (R)0);
+    };
+    if (PF && t < R2 && blockIdx.z * vpc < v1) load(blockIdx.z * vpc);
     for (int v = blockIdx.z * vpc; v < v1; ++v) {
         if (t < R2) {
-            const C* Wv = W + (size_t)v * 3 * n + base;
-            C g[3][R1];
-#pragma unroll
-            for (int l = 0; l < 3; ++l)
-#pragma unroll
-                for (int t1 = 0; t1 < R1; ++t1)
-                    g[l][t1] = valid ? Wv[(size_t)l * n + (size_t)(t + R2 * t1) * plane] : mk((R)0, (R)0);
+            if (!PF) load(v);
 #pragma unroll
             for (int l = 0; l < 3; ++l) {
 #pragma unroll
@@ -230,6 +248,7 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
                 for (int k1 = 0; k1 < R1; ++k1)
                     Y[(l * L + k1 * R2 + t) * TP + pp] = twid<false>(g[l][k1], T.tw, t, k1);
             }
+            if (PF && v + 1 < v1) load(v + 1);
         }
         __syncthreads();
         if (t < R1) {
@@ -265,7 +284,7 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
 // mode 0: full apply; mode 1: lift x = B^{-1} T (...) (stops after the
 // inverse x transform, applies the D_a1 twist and lift_scale).
 // ---------------------------------------------------------------------------
-constexpr int kXYThreads = 256;
+constexpr int kXYThreads = 256, kXYThreadsWide = 512;
 
 template <typename R, int LX, int LY>
 struct XYLayout {
@@ -280,14 +299,14 @@ struct XYLayout {
     static constexpr size_t bytes = f2_off + LX * sizeof(F);
 };
 
-template <typename R, int LX, int LY>
-__global__ void __launch_bounds__(kXYThreads)
-k_xy3(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode, R lift_scale) {
+template <typename R, int LX, int LY, int NT>
+__device__ __forceinline__ void xy3_plane(const KParams<R>& P, typename cpx<R>::T* __restrict__ W, int mode,
+                                          R lift_scale) {
     using C = typename cpx<R>::T;
     using F = typename FracT<R>::T;
     using Lay = XYLayout<R, LX, LY>;
     constexpr int RX1 = Sp<LX>::R1, RX2 = Sp<LX>::R2, RY1 = Sp<LY>::R1, RY2 = Sp<LY>::R2;
-    constexpr int NT = kXYThreads, S = Lay::S, NP = LX * LY;
+    constexpr int S = Lay::S, NP = LX * LY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* X = reinterpret_cast<C*>(smem_raw + Lay::x_off);
     R* ibs = reinterpret_cast<R*>(smem_raw + Lay::ib_off);
@@ -437,6 +456,25 @@ k_xy3(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode, R lift_scale) 
     }
 }
 
+// 256 threads: the register allocator's own choice; 512 threads: as many blocks per SM
+// as shared memory allows, at most 3
+template <typename R, int LX, int LY, int NT> struct XYOcc {
+    static constexpr int by_smem = (int)((227u * 1024u) / XYLayout<R, LX, LY>::bytes);
+    static constexpr int value = by_smem < 1 ? 1 : (by_smem > 3 ? 3 : by_smem);
+};
+
+template <typename R, int LX, int LY>
+__global__ void __launch_bounds__(kXYThreads)
+k_xy3(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode, R lift_scale) {
+    xy3_plane<R, LX, LY, kXYThreads>(P, W, mode, lift_scale);
+}
+
+template <typename R, int LX, int LY>
+__global__ void __launch_bounds__(kXYThreadsWide, (XYOcc<R, LX, LY, kXYThreadsWide>::value))
+k_xy3w(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode, R lift_scale) {
+    xy3_plane<R, LX, LY, kXYThreadsWide>(P, W, mode, lift_scale);
+}
+
 // ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
@@ -445,13 +483,13 @@ constexpr int kZTP = 16;
 template <typename R, int L>
 size_t z3_dyn_smem() { return (size_t)3 * L * kZTP * sizeof(typename cpx<R>::T); }
 
-template <typename R, int L>
+template <typename R, int L, bool PF>
 fame_status launch_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
                       typename cpx<R>::T* out, int m, bool zin, int vpc_req, cudaStream_t st) {
     const int n1 = c->plan.n[0], n2 = c->plan.n[1];
     constexpr int NT = kZTP * Sp<L>::RMAX;
     const size_t smem = z3_dyn_smem<R, L>();
-    const void* fn = zin ? (const void*)k_zin3<R, L, kZTP> : (const void*)k_zout3<R, L, kZTP>;
+    const void* fn = zin ? (const void*)k_zin3<R, L, kZTP, PF> : (const void*)k_zout3<R, L, kZTP, PF>;
     if (smem + sizeof(ZTile<R, L, kZTP>) > 48 * 1024)
         FAME_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long tiles = (long long)((n1 + kZTP - 1) / kZTP) * n2;
@@ -464,27 +502,35 @@ fame_status launch_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T
     ProfScope ps(zin ? K_ZIN : K_ZOUT, sizeof(R) == 8, st, 5.0 * nm * sizeof(typename cpx<R>::T),
                  3 * nm * 5.0 * std::log2((double)L) + 60.0 * nm);
     if (zin)
-        k_zin3<R, L, kZTP><<<grid, NT, smem, st>>>(P, in, out, m, vpc);
+        k_zin3<R, L, kZTP, PF><<<grid, NT, smem, st>>>(P, in, out, m, vpc);
     else
-        k_zout3<R, L, kZTP><<<grid, NT, smem, st>>>(P, in, out, m, vpc);
+        k_zout3<R, L, kZTP, PF><<<grid, NT, smem, st>>>(P, in, out, m, vpc);
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
     return FAME_OK;
 }
 
-template <typename R, int LX, int LY>
+template <typename R, int LX, int LY, int NT>
 fame_status launch_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int m, int mode,
                        R lift_scale, cudaStream_t st) {
     using C = typename cpx<R>::T;
     const size_t smem = XYLayout<R, LX, LY>::bytes;
+    const void* fn;
+    if constexpr (NT == kXYThreads)
+        fn = (const void*)k_xy3<R, LX, LY>;
+    else
+        fn = (const void*)k_xy3w<R, LX, LY>;
     if (smem > 48 * 1024)
-        FAME_CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_xy3<R, LX, LY>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FAME_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const double nm = (double)c->n * m;
     const double lg = std::log2((double)LX) + std::log2((double)LY);
     ProfScope ps(K_XY, sizeof(R) == 8, st, 2.0 * 3 * nm * sizeof(C) + 3.0 * c->n * sizeof(R),
                  3 * nm * 5.0 * (mode == 0 ? 2.0 : 1.0) * lg);
-    k_xy3<R, LX, LY><<<(unsigned)(3LL * m * c->plan.n[2]), kXYThreads, smem, st>>>(P, W, mode, lift_scale);
+    const unsigned blocks = (unsigned)(3LL * m * c->plan.n[2]);
+    if constexpr (NT == kXYThreads)
+        k_xy3<R, LX, LY><<<blocks, NT, smem, st>>>(P, W, mode, lift_scale);
+    else
+        k_xy3w<R, LX, LY><<<blocks, NT, smem, st>>>(P, W, mode, lift_scale);
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());
     return FAME_OK;
@@ -499,32 +545,48 @@ bool xy3_supported(int n1, int n2) {
            (n1 == 80 && n2 == 96);
 }
 
-template <typename R>
-fame_status run_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
-                   typename cpx<R>::T* out, int m, bool zin, int vpc, cudaStream_t st) {
+template <typename R, bool PF>
+fame_status run_z3_len(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
+                       typename cpx<R>::T* out, int m, bool zin, int vpc, cudaStream_t st) {
     switch (c->plan.n[2]) {
-        case 16: return launch_z3<R, 16>(c, P, in, out, m, zin, vpc, st);
-        case 32: return launch_z3<R, 32>(c, P, in, out, m, zin, vpc, st);
-        case 48: return launch_z3<R, 48>(c, P, in, out, m, zin, vpc, st);
-        case 64: return launch_z3<R, 64>(c, P, in, out, m, zin, vpc, st);
-        case 80: return launch_z3<R, 80>(c, P, in, out, m, zin, vpc, st);
-        case 96: return launch_z3<R, 96>(c, P, in, out, m, zin, vpc, st);
+        case 16: return launch_z3<R, 16, PF>(c, P, in, out, m, zin, vpc, st);
+        case 32: return launch_z3<R, 32, PF>(c, P, in, out, m, zin, vpc, st);
+        case 48: return launch_z3<R, 48, PF>(c, P, in, out, m, zin, vpc, st);
+        case 64: return launch_z3<R, 64, PF>(c, P, in, out, m, zin, vpc, st);
+        case 80: return launch_z3<R, 80, PF>(c, P, in, out, m, zin, vpc, st);
+        case 96: return launch_z3<R, 96, PF>(c, P, in, out, m, zin, vpc, st);
         default: return set_err(c, FAME_E_ARG, "fixed-length Z pass: unsupported n3");
     }
 }
 
 template <typename R>
+fame_status run_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
+                   typename cpx<R>::T* out, int m, bool zin, int vpc, bool prefetch, cudaStream_t st) {
+    return prefetch ? run_z3_len<R, true>(c, P, in, out, m, zin, vpc, st)
+                    : run_z3_len<R, false>(c, P, in, out, m, zin, vpc, st);
+}
+
+// planes with at least 512 work items per radix step also have a 512-thread form
+bool xy3_wide_supported(int n1, int n2) { return xy3_supported(n1, n2) && n1 * n2 >= 4096; }
+
+template <typename R>
 fame_status run_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int m, int mode,
-                    R lift_scale, cudaStream_t st) {
+                    R lift_scale, bool wide, cudaStream_t st) {
     const int n1 = c->plan.n[0], n2 = c->plan.n[1];
-    if (n1 == 80 && n2 == 96) return launch_xy3<R, 80, 96>(c, P, W, m, mode, lift_scale, st);
+    if (wide) {
+        if (n1 == 80 && n2 == 96) return launch_xy3<R, 80, 96, kXYThreadsWide>(c, P, W, m, mode, lift_scale, st);
+        if (n1 == 64 && n2 == 64) return launch_xy3<R, 64, 64, kXYThreadsWide>(c, P, W, m, mode, lift_scale, st);
+        if (n1 == 96 && n2 == 96) return launch_xy3<R, 96, 96, kXYThreadsWide>(c, P, W, m, mode, lift_scale, st);
+        return set_err(c, FAME_E_ARG, "fixed-length XY pass, 512 threads: unsupported (n1, n2)");
+    }
+    if (n1 == 80 && n2 == 96) return launch_xy3<R, 80, 96, kXYThreads>(c, P, W, m, mode, lift_scale, st);
     if (n1 == n2) {
         switch (n1) {
-            case 16: return launch_xy3<R, 16, 16>(c, P, W, m, mode, lift_scale, st);
-            case 32: return launch_xy3<R, 32, 32>(c, P, W, m, mode, lift_scale, st);
-            case 48: return launch_xy3<R, 48, 48>(c, P, W, m, mode, lift_scale, st);
-            case 64: return launch_xy3<R, 64, 64>(c, P, W, m, mode, lift_scale, st);
-            case 96: return launch_xy3<R, 96, 96>(c, P, W, m, mode, lift_scale, st);
+            case 16: return launch_xy3<R, 16, 16, kXYThreads>(c, P, W, m, mode, lift_scale, st);
+            case 32: return launch_xy3<R, 32, 32, kXYThreads>(c, P, W, m, mode, lift_scale, st);
+            case 48: return launch_xy3<R, 48, 48, kXYThreads>(c, P, W, m, mode, lift_scale, st);
+            case 64: return launch_xy3<R, 64, 64, kXYThreads>(c, P, W, m, mode, lift_scale, st);
+            case 96: return launch_xy3<R, 96, 96, kXYThreads>(c, P, W, m, mode, lift_scale, st);
             default: break;
         }
     }
@@ -532,5 +594,6 @@ fame_status run_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int
 }
 
 template fame_status run_z3<float>(fame_ctx*, const KParams<float>&, const float2*, float2*, int, bool, int,
-                                   cudaStream_t);
-template fame_status run_xy3<float>(fame_ctx*, const KParams<float>&, float2*, int, int, float, cudaStream_t);
+                                   bool, cudaStream_t);
+template fame_status run_xy3<float>(fame_ctx*, const KParams<float>&, float2*, int, int, float, bool,
+                                    cudaStream_t);

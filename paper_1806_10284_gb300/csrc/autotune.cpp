@@ -8,8 +8,11 @@
 
 namespace {
 
+constexpr int kZFamilies = 4, kXYFamilies = 5;
+
 fame_status check_plan(fame_ctx* c, int dtype, const fame_apply_plan& p) {
-    if (p.z_kernel < 0 || p.z_kernel > 3 || p.xy_kernel < 0 || p.xy_kernel > 4 || p.vectors_per_block < 0 ||
+    if (p.z_kernel < 0 || p.z_kernel > kZFamilies || p.xy_kernel < 0 || p.xy_kernel > kXYFamilies ||
+        p.vectors_per_block < 0 ||
         p.vectors_per_block > 4096)
         return set_err(c, FAME_E_ARG, "apply plan field out of range");
     if (p.z_kernel && !apply_zfam_available(c, dtype, p.z_kernel, 1))
@@ -91,7 +94,7 @@ fame_status fame_autotune(fame_ctx* c, int m, int dtype, double* best_ms, void* 
     void* y = buf;
     void* Ay = static_cast<char*>(buf) + bytes;
     // Z family and vectors per block first (XY automatic), then the XY family
-    for (int zf = 1; s == FAME_OK && zf <= 3; ++zf) {
+    for (int zf = 1; s == FAME_OK && zf <= kZFamilies; ++zf) {
         if (!apply_zfam_available(c, dtype, zf, m)) continue;
         for (int vpc : {1, 2, 4, 8, 16}) {
             if (vpc > m && vpc > 1) break;
@@ -101,7 +104,7 @@ fame_status fame_autotune(fame_ctx* c, int m, int dtype, double* best_ms, void* 
             if (t < best_t) { best_t = t; best = c->apply_plan[dtype]; }
         }
     }
-    for (int xf = 1; s == FAME_OK && xf <= 4; ++xf) {
+    for (int xf = 1; s == FAME_OK && xf <= kXYFamilies; ++xf) {
         if (!apply_xyfam_available(c, dtype, xf)) continue;
         c->apply_plan[dtype] = ApplyPlan{best.zfam, xf, best.vpc};
         double t = 0.0;
@@ -110,7 +113,7 @@ fame_status fame_autotune(fame_ctx* c, int m, int dtype, double* best_ms, void* 
     }
     if (best.xyfam == 0 && s == FAME_OK) {
         // automatic XY kept: record the family it resolves to
-        for (int xf = 1; xf <= 4; ++xf)
+        for (int xf = 1; xf <= kXYFamilies; ++xf)
             if (apply_xyfam_available(c, dtype, xf)) { best.xyfam = xf; break; }
     }
     c->apply_plan[dtype] = (s == FAME_OK) ? best : saved;

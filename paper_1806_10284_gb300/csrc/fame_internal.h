@@ -215,10 +215,11 @@ bool z3_supported(int L);
 bool xy3_supported(int n1, int n2);
 template <typename R>
 fame_status run_z3(fame_ctx* c, const KParams<R>& P, const typename cpx<R>::T* in,
-                   typename cpx<R>::T* out, int m, bool zin, int vpc, cudaStream_t st);
+                   typename cpx<R>::T* out, int m, bool zin, int vpc, bool prefetch, cudaStream_t st);
 template <typename R>
 fame_status run_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int m, int mode,
-                    R lift_scale, cudaStream_t st);
+                    R lift_scale, bool wide, cudaStream_t st);
+bool xy3_wide_supported(int n1, int n2);
 fame_status run_basis_mask(fame_ctx* c);
 fame_status run_twist_tables(fame_ctx* c);
 

@@ -781,6 +781,7 @@ bool apply_zfam_available(const fame_ctx* c, int dtype, int zfam, int m) {
         case 1: return dtype == FAME_C64 && z3_supported(n3);
         case 2: return dtype == FAME_C64 ? z2_config<float>(c, m).ok : z2_config<double>(c, m).ok;
         case 3: return true;
+        case 4: return dtype == FAME_C64 && z3_supported(n3);
         default: return false;
     }
 }
@@ -794,6 +795,7 @@ bool apply_xyfam_available(const fame_ctx* c, int dtype, int xyfam) {
                        (dtype == FAME_C64 ? xy2_smem<float>(n1, n2) : xy2_smem<double>(n1, n2)) <= kSmemCap;
         case 3: return (size_t)(n1 + n2 + 2 * n1 * n2) * esz <= kSmemCap;
         case 4: return true;
+        case 5: return dtype == FAME_C64 && xy3_wide_supported(n1, n2);
         default: return false;
     }
 }
@@ -812,7 +814,7 @@ static fame_status xy_stage(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T
     if (fam == 0 || !apply_xyfam_available(c, dtype, fam))
         for (fam = 1; !apply_xyfam_available(c, dtype, fam); ++fam) {}
     if constexpr (std::is_same<R, float>::value) {
-        if (fam == 1) return run_xy3<R>(c, P, W, m, mode, lift_scale, st);
+        if (fam == 1 || fam == 5) return run_xy3<R>(c, P, W, m, mode, lift_scale, fam == 5, st);
     }
     const size_t smem2 = xy2_smem<R>(n1, n2);
     if (fam == 2) {
@@ -899,7 +901,7 @@ static fame_status z_pass(fame_ctx* c, const KParams<R>& P, const typename cpx<R
     const int vpc_req = ap.vpc > 0 ? std::min(ap.vpc, m) : 0;
     fame_status s;
     if constexpr (std::is_same<R, float>::value) {
-        if (fam == 1) return run_z3<R>(c, P, in, out, m, zin, vpc_req, st);
+        if (fam == 1 || fam == 4) return run_z3<R>(c, P, in, out, m, zin, vpc_req, fam == 1, st);
     }
     const int kind = zin ? K_ZIN : K_ZOUT;
     const double bytes = 5.0 * nm * sizeof(C), flops = 3 * nm * 5.0 * lg2(n3) + 60.0 * nm;

@@ -241,8 +241,8 @@ def test_every_apply_plan_matches_oracle(prec):
     refs = [apply_Ar(lat, y[j].reshape((2,) + lat.shape), invB).ravel() for j in range(m)]
     yt = torch.as_tensor(y, dtype=dt, device="cuda")
     tried = 0
-    for z in (1, 2, 3):
-        for xy in (1, 2, 3, 4):
+    for z in (1, 2, 3, 4):
+        for xy in (1, 2, 3, 4, 5):
             for vpc in (1, 2):
                 try:
                     ctx.set_apply_plan(dtype, z, xy, vpc)
@@ -252,8 +252,43 @@ def test_every_apply_plan_matches_oracle(prec):
                 for j in range(m):
                     assert _rel(got[j], refs[j]) < (TOL64 if prec == "c128" else TOL32), (z, xy, vpc, j)
                 tried += 1
-    assert tried >= (16 if prec == "c64" else 9)
+    assert tried >= (24 if prec == "c64" else 9)
     ctx.set_apply_plan(dtype)
+
+
+@pytest.mark.parametrize("name,n", [("fcc64", (64, 64, 16)),   # XY 64x64, Z 16
+                                    ("mono80", (80, 96, 16)),  # XY 80x96
+                                    ("bcc96", (96, 96, 8)),    # XY 96x96, generic Z
+                                    ("bcc96", (16, 16, 32)),   # Z 32
+                                    ("mono80", (16, 16, 48)),  # Z 48
+                                    ("tri192", (16, 16, 64)),  # Z 64
+                                    ("sc16", (16, 16, 80)),    # Z 80
+                                    ("hex96", (16, 16, 96))])  # Z 96
+def test_fixed_length_variants_match_oracle(name, n):
+    """The 256- and 512-thread fixed-length XY pass and the fixed-length Z passes with
+    and without next-vector prefetch give the oracle's A_r y, with block sizes that
+    leave a partial last block of vectors."""
+    lat, ctx, invB, rng = _setup(name, n, seed=4)
+    m = 5
+    y = rng.standard_normal((m, 2 * lat.n)) + 1j * rng.standard_normal((m, 2 * lat.n))
+    refs = [apply_Ar(lat, y[j].reshape((2,) + lat.shape), invB).ravel() for j in range(m)]
+    yt = torch.as_tensor(y, dtype=torch.complex64, device="cuda")
+    zs = (1, 4) if n[2] != 8 else (0,)     # no fixed-length Z pass of length 8
+    tried = 0
+    for z in zs:
+        for xy in (1, 5):
+            for vpc in (1, 2, 4):
+                try:
+                    ctx.set_apply_plan(fame.FAME_C64, z, xy, vpc)
+                except fame.FameError:
+                    continue
+                got = ctx.apply(yt).cpu().numpy()
+                for j in range(m):
+                    assert _rel(got[j], refs[j]) < TOL32, (z, xy, vpc, j)
+                tried += 1
+    wide = n[0] * n[1] >= 4096             # the 512-thread XY form exists
+    assert tried == 3 * len(zs) * (2 if wide else 1)
+    ctx.set_apply_plan(fame.FAME_C64)
 
 
 def test_autotune_and_plan_cache(tmp_path):
@@ -261,7 +296,7 @@ def test_autotune_and_plan_cache(tmp_path):
     cache = str(tmp_path / "plans.json")
     first = ctx.autotune(6, fame.FAME_C64, cache=cache)
     assert not first["cached"] and first["ms"] > 0
-    assert first["z_kernel"] in (1, 2, 3) and first["xy_kernel"] in (1, 2, 3, 4)
+    assert first["z_kernel"] in (1, 2, 3, 4) and first["xy_kernel"] in (1, 2, 3, 4, 5)
     y = rng.standard_normal((2, 2 * lat.n)) + 1j * rng.standard_normal((2, 2 * lat.n))
     got = ctx.apply(torch.as_tensor(y, dtype=torch.complex64, device="cuda")).cpu().numpy()
     for j in range(2):
