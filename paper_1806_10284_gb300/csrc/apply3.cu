@@ -41,10 +41,10 @@ template <int L> struct Sp {
     static constexpr int RMAX = R1 > R2 ? R1 : R2;
 };
 // Z-pass blocks per SM asked of the register allocator: about 640 resident threads
-// where that fits without spills, else about 512 (the prefetching Z-in holds a second
+// where that fits without spills, else about 512 (the prefetching forms hold a second
 // vector's inputs in registers)
 template <int L, int NT, bool OUT, bool PF = false> struct ZOcc {
-    static constexpr int threads = ((L == 64 && !OUT && !PF) || L <= 32) ? 640 : 512;
+    static constexpr int threads = ((L == 64 && !OUT && !PF) || (L <= 32 && !(OUT && PF))) ? 640 : 512;
     static constexpr int value = threads / NT > 0 ? threads / NT : 1;
 };
 
@@ -135,7 +135,6 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
     const int n1 = P.n1, n2 = P.n2;
     const size_t n = (size_t)n1 * n2 * L, plane = (size_t)n1 * n2;
     const int q = blockIdx.y, p0 = blockIdx.x * TP;
-    ztile_setup<R, L, TP>(T, P, q, p0);
     const int pp = threadIdx.x % TP, t = threadIdx.x / TP, p = p0 + pp;
     const bool valid = p < n1;
     const size_t base = (size_t)q * n1 + p;
@@ -152,7 +151,9 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
             a2[t1] = valid ? yv[n + off] : mk((R)0, (R)0);
         }
     };
+    // with PF the first vector's loads are in flight while the tile tables are built
     if (PF && t < R2 && blockIdx.z * vpc < v1) load(blockIdx.z * vpc);
+    ztile_setup<R, L, TP>(T, P, q, p0);
     for (int v = blockIdx.z * vpc; v < v1; ++v) {
         if (t < R2) {
             if (!PF) load(v);
@@ -208,7 +209,7 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
 // Z-out: conj D_a3 twist -> forward z-DFT -> Pi_r^H contraction, Sigma_r.
 // ---------------------------------------------------------------------------
 template <typename R, int L, int TP, bool PF>
-__global__ void __launch_bounds__(TP * Sp<L>::RMAX, ZOcc<L, TP * Sp<L>::RMAX, true>::value)
+__global__ void __launch_bounds__(TP * Sp<L>::RMAX, (ZOcc<L, TP * Sp<L>::RMAX, true, PF>::value))
 k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>::T* __restrict__ out,
         int m, int vpc) {
     using C = typename cpx<R>::T;
@@ -219,7 +220,6 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
     const int n1 = P.n1, n2 = P.n2;
     const size_t n = (size_t)n1 * n2 * L, plane = (size_t)n1 * n2;
     const int q = blockIdx.y, p0 = blockIdx.x * TP;
-    ztile_setup<R, L, TP>(T, P, q, p0);
     const int pp = threadIdx.x % TP, t = threadIdx.x / TP, p = p0 + pp;
     const bool valid = p < n1;
     const size_t base = (size_t)q * n1 + p;
@@ -235,7 +235,9 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
             for (int t1 = 0; t1 < R1; ++t1)
                 g[l][t1] = valid ? Wv[(size_t)l * n + (size_t)(t + R2 * t1) * plane] : mk((R)0, (R)0);
     };
+    // with PF the first vector's loads are in flight while the tile tables are built
     if (PF && t < R2 && blockIdx.z * vpc < v1) load(blockIdx.z * vpc);
+    ztile_setup<R, L, TP>(T, P, q, p0);
     for (int v = blockIdx.z * vpc; v < v1; ++v) {
         if (t < R2) {
             if (!PF) load(v);

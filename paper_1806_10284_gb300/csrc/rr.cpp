@@ -2,7 +2,9 @@
 // block eigensolver.  Householder reduction of a Hermitian matrix to real
 // symmetric tridiagonal form (with a diagonal unitary phase), then implicit
 // symmetric QR with the Wilkinson shift (Golub and Van Loan, Matrix
-// Computations, Sections 8.3.1-8.3.3).  The generalized pair (GA, GB) is
+// Computations, Sections 8.3.1-8.3.3).  The reflectors are kept rather than
+// multiplied out, and only the wanted eigenvectors are carried back through
+// them: the Rayleigh-Ritz step needs the m smallest of 3m.  The generalized pair (GA, GB) is
 // reduced to a standard problem on a GB-orthonormal basis built from the
 // Cholesky factor of the diagonally scaled GB when it is well conditioned, else
 // from the eigen-decomposition of the scaled GB, dropping numerically dependent
@@ -19,9 +21,54 @@ using cd = std::complex<double>;
 
 namespace {
 
-// column-major k x k complex matrix helpers
-inline cd& at(std::vector<cd>& A, int k, int i, int j) { return A[(size_t)j * k + i]; }
+// sum_i conj(a_i) b_i and sum_i a_i b_i over split complex vectors, with four
+// independent partial sums so that the additions pipeline
+inline void dot_conj(int n, const double* ar, const double* ai, const double* br, const double* bi, double& sr,
+                     double& si) {
+    double r0 = 0, r1 = 0, r2 = 0, r3 = 0, i0 = 0, i1 = 0, i2 = 0, i3 = 0;
+    int t = 0;
+    for (; t + 1 < n; t += 2) {
+        r0 += ar[t] * br[t];
+        r1 += ai[t] * bi[t];
+        i0 += ar[t] * bi[t];
+        i1 -= ai[t] * br[t];
+        r2 += ar[t + 1] * br[t + 1];
+        r3 += ai[t + 1] * bi[t + 1];
+        i2 += ar[t + 1] * bi[t + 1];
+        i3 -= ai[t + 1] * br[t + 1];
+    }
+    if (t < n) {
+        r0 += ar[t] * br[t] + ai[t] * bi[t];
+        i0 += ar[t] * bi[t] - ai[t] * br[t];
+    }
+    sr = (r0 + r1) + (r2 + r3);
+    si = (i0 + i1) + (i2 + i3);
+}
+inline void dot_plain(int n, const double* ar, const double* ai, const double* br, const double* bi, double& sr,
+                      double& si) {
+    double r0 = 0, r1 = 0, r2 = 0, r3 = 0, i0 = 0, i1 = 0, i2 = 0, i3 = 0;
+    int t = 0;
+    for (; t + 1 < n; t += 2) {
+        r0 += ar[t] * br[t];
+        r1 -= ai[t] * bi[t];
+        i0 += ar[t] * bi[t];
+        i1 += ai[t] * br[t];
+        r2 += ar[t + 1] * br[t + 1];
+        r3 -= ai[t + 1] * bi[t + 1];
+        i2 += ar[t + 1] * bi[t + 1];
+        i3 += ai[t + 1] * br[t + 1];
+    }
+    if (t < n) {
+        r0 += ar[t] * br[t] - ai[t] * bi[t];
+        i0 += ar[t] * bi[t] + ai[t] * br[t];
+    }
+    sr = (r0 + r1) + (r2 + r3);
+    si = (i0 + i1) + (i2 + i3);
+}
 
+// implicit symmetric QR on the tridiagonal (d, e) with the Wilkinson shift from the
+// trailing 2 x 2 block, deflation where |e_i| <= eps (|d_i| + |d_i+1|); the
+// rotations are accumulated into Z
 void tridiag_qr(int k, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
     // d[0..k-1] diagonal, e[0..k-2] off-diagonal; Z (k x k, column-major) accumulates rotations
     const double eps = 2.220446049250313e-16;
@@ -75,63 +122,94 @@ void herm_eig(int k, const double* Ain, double* w, double* Vout) { herm_eig_n(k,
 
 // as herm_eig, eigenvectors of the nvec smallest eigenvalues only (all k eigenvalues)
 void herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec) {
-    std::vector<cd> A((size_t)k * k), Q((size_t)k * k, cd(0.0));
-    for (size_t i = 0; i < (size_t)k * k; ++i) A[i] = cd(Ain[2 * i], Ain[2 * i + 1]);
-    // Hermitise (use the lower triangle as given)
-    for (int j = 0; j < k; ++j) {
-        at(A, k, j, j) = cd(at(A, k, j, j).real(), 0.0);
-        for (int i = j + 1; i < k; ++i) at(A, k, j, i) = std::conj(at(A, k, i, j));
-    }
-    for (int i = 0; i < k; ++i) at(Q, k, i, i) = 1.0;
-    std::vector<cd> v(k), p(k), qv(k);
+    // real and imaginary parts, column-major, lower triangle used; the reflector
+    // H_j = I - beta_j v_j v_j^H maps column j below the diagonal onto -phase alpha e_1
+    std::vector<double> ar((size_t)k * k), ai((size_t)k * k);
+    for (int j = 0; j < k; ++j)
+        for (int i = j; i < k; ++i) {
+            ar[(size_t)j * k + i] = Ain[2 * ((size_t)j * k + i)];
+            ai[(size_t)j * k + i] = (i == j) ? 0.0 : Ain[2 * ((size_t)j * k + i) + 1];
+        }
+    auto AR = [&](int i, int j) -> double& { return ar[(size_t)j * k + i]; };
+    auto AI = [&](int i, int j) -> double& { return ai[(size_t)j * k + i]; };
+    std::vector<double> vr((size_t)k * k, 0.0), vi((size_t)k * k, 0.0), betas(k, 0.0);   // reflectors
+    std::vector<double> pr(k), pi(k);
     for (int j = 0; j + 2 < k; ++j) {
-        const int len = k - j - 1;
+        const int o = j + 1;
         double alpha = 0.0;
-        for (int i = 0; i < len; ++i) alpha += std::norm(at(A, k, j + 1 + i, j));
+        for (int i = o; i < k; ++i) alpha += AR(i, j) * AR(i, j) + AI(i, j) * AI(i, j);
         alpha = std::sqrt(alpha);
         if (alpha == 0.0) continue;
-        const cd x0 = at(A, k, j + 1, j);
-        const cd ph = (std::abs(x0) == 0.0) ? cd(1.0) : x0 / std::abs(x0);
-        for (int i = 0; i < len; ++i) v[i] = at(A, k, j + 1 + i, j);
-        v[0] += ph * alpha;
+        const double x0r = AR(o, j), x0i = AI(o, j), ax0 = std::hypot(x0r, x0i);
+        const double phr = (ax0 == 0.0) ? 1.0 : x0r / ax0, phi = (ax0 == 0.0) ? 0.0 : x0i / ax0;
+        double* v_r = &vr[(size_t)j * k];
+        double* v_i = &vi[(size_t)j * k];
+        for (int i = o; i < k; ++i) { v_r[i] = AR(i, j); v_i[i] = AI(i, j); }
+        v_r[o] += phr * alpha;
+        v_i[o] += phi * alpha;
         double vv = 0.0;
-        for (int i = 0; i < len; ++i) vv += std::norm(v[i]);
+        for (int i = o; i < k; ++i) vv += v_r[i] * v_r[i] + v_i[i] * v_i[i];
         if (vv == 0.0) continue;
         const double beta = 2.0 / vv;
-        // p = beta * A22 v
-        for (int i = 0; i < len; ++i) {
-            cd s = 0.0;
-            for (int t = 0; t < len; ++t) s += at(A, k, j + 1 + i, j + 1 + t) * v[t];
-            p[i] = beta * s;
+        betas[j] = beta;
+        // p = beta A22 v, A22 Hermitian from its lower triangle
+        for (int i = o; i < k; ++i) { pr[i] = 0.0; pi[i] = 0.0; }
+        for (int t = o; t < k; ++t) {
+            const double vtr = v_r[t], vti = v_i[t];
+            // diagonal
+            pr[t] += AR(t, t) * vtr;
+            pi[t] += AR(t, t) * vti;
+            const double* cr = &ar[(size_t)t * k];
+            const double* ci = &ai[(size_t)t * k];
+            for (int i = t + 1; i < k; ++i) {                // p_i += A(i,t) v_t
+                pr[i] += cr[i] * vtr - ci[i] * vti;
+                pi[i] += cr[i] * vti + ci[i] * vtr;
+            }
+            double sr, si;                                    // p_t += sum_i conj(A(i,t)) v_i
+            dot_conj(k - t - 1, cr + t + 1, ci + t + 1, v_r + t + 1, v_i + t + 1, sr, si);
+            pr[t] += sr;
+            pi[t] += si;
         }
-        cd K = 0.0;
-        for (int i = 0; i < len; ++i) K += std::conj(v[i]) * p[i];
-        K *= 0.5 * beta;
-        for (int i = 0; i < len; ++i) qv[i] = p[i] - K * v[i];
-        for (int t = 0; t < len; ++t)
-            for (int i = 0; i < len; ++i)
-                at(A, k, j + 1 + i, j + 1 + t) -= v[i] * std::conj(qv[t]) + qv[i] * std::conj(v[t]);
-        at(A, k, j + 1, j) = -ph * alpha;
-        at(A, k, j, j + 1) = std::conj(-ph * alpha);
-        for (int i = 1; i < len; ++i) { at(A, k, j + 1 + i, j) = 0.0; at(A, k, j, j + 1 + i) = 0.0; }
-        // Q <- Q H on columns j+1..k-1
-        for (int r = 0; r < k; ++r) {
-            cd s = 0.0;
-            for (int t = 0; t < len; ++t) s += at(Q, k, r, j + 1 + t) * v[t];
-            s *= beta;
-            for (int t = 0; t < len; ++t) at(Q, k, r, j + 1 + t) -= s * std::conj(v[t]);
+        double Kr = 0.0, Ki = 0.0;                          // K = (beta/2) v^H p (p before scaling by beta)
+        for (int i = o; i < k; ++i) {
+            pr[i] *= beta;
+            pi[i] *= beta;
+            Kr += v_r[i] * pr[i] + v_i[i] * pi[i];
+            Ki += v_r[i] * pi[i] - v_i[i] * pr[i];
         }
+        Kr *= 0.5 * beta;
+        Ki *= 0.5 * beta;
+        for (int i = o; i < k; ++i) {                       // q = p - K v (stored in p)
+            const double qr = pr[i] - (Kr * v_r[i] - Ki * v_i[i]);
+            const double qi = pi[i] - (Kr * v_i[i] + Ki * v_r[i]);
+            pr[i] = qr;
+            pi[i] = qi;
+        }
+        for (int t = o; t < k; ++t) {                       // lower triangle: A -= v q^H + q v^H
+            const double vtr = v_r[t], vti = v_i[t], qtr = pr[t], qti = pi[t];
+            double* cr = &ar[(size_t)t * k];
+            double* ci = &ai[(size_t)t * k];
+            for (int i = t; i < k; ++i) {
+                cr[i] -= (v_r[i] * qtr + v_i[i] * qti) + (pr[i] * vtr + pi[i] * vti);
+                ci[i] -= (v_i[i] * qtr - v_r[i] * qti) + (pi[i] * vtr - pr[i] * vti);
+            }
+        }
+        AR(o, j) = -phr * alpha;
+        AI(o, j) = -phi * alpha;
     }
-    // real tridiagonal through the diagonal phase D: T_real = D^H T D
-    std::vector<double> d(k), e(std::max(k - 1, 1));
-    std::vector<cd> ph(k);
-    ph[0] = 1.0;
-    for (int i = 0; i < k; ++i) d[i] = at(A, k, i, i).real();
+    // real tridiagonal through the diagonal phase: T_real = D^H T D
+    std::vector<double> d(k), e(std::max(k - 1, 1), 0.0), phr(k), phi(k);
+    phr[0] = 1.0;
+    phi[0] = 0.0;
+    for (int i = 0; i < k; ++i) d[i] = AR(i, i);
     for (int i = 0; i + 1 < k; ++i) {
-        const cd ec = at(A, k, i + 1, i);
-        const double m = std::abs(ec);
+        const double er = AR(i + 1, i), ei = AI(i + 1, i), m = std::hypot(er, ei);
         e[i] = m;
-        ph[i + 1] = (m == 0.0) ? ph[i] : ph[i] * ec / m;
+        if (m == 0.0) { phr[i + 1] = phr[i]; phi[i + 1] = phi[i]; }
+        else {
+            phr[i + 1] = (phr[i] * er - phi[i] * ei) / m;
+            phi[i + 1] = (phr[i] * ei + phi[i] * er) / m;
+        }
     }
     std::vector<double> Z((size_t)k * k, 0.0);
     for (int i = 0; i < k; ++i) Z[(size_t)i * k + i] = 1.0;
@@ -139,15 +217,28 @@ void herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec) {
     std::vector<int> order(k);
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });
-    // V = Q D Z
-    for (int jj = 0; jj < k; ++jj) w[jj] = d[order[jj]];
-    for (int jj = 0; jj < nvec; ++jj) {
-        const int j = order[jj];
-        for (int r = 0; r < k; ++r) {
-            cd s = 0.0;
-            for (int t = 0; t < k; ++t) s += at(Q, k, r, t) * ph[t] * Z[(size_t)j * k + t];
-            Vout[2 * ((size_t)jj * k + r)] = s.real();
-            Vout[2 * ((size_t)jj * k + r) + 1] = s.imag();
+    for (int i = 0; i < k; ++i) w[i] = d[order[i]];
+    // V = H_0 ... H_{k-3} D Z: phase, then the reflectors in reverse order
+    std::vector<double> yr(k), yi(k);
+    for (int c = 0; c < nvec; ++c) {
+        const double* z = &Z[(size_t)order[c] * k];
+        for (int i = 0; i < k; ++i) { yr[i] = phr[i] * z[i]; yi[i] = phi[i] * z[i]; }
+        for (int j = k - 3; j >= 0; --j) {
+            if (betas[j] == 0.0) continue;
+            const double* v_r = &vr[(size_t)j * k];
+            const double* v_i = &vi[(size_t)j * k];
+            double sr, si;                                    // s = v^H y
+            dot_conj(k - j - 1, v_r + j + 1, v_i + j + 1, yr.data() + j + 1, yi.data() + j + 1, sr, si);
+            sr *= betas[j];
+            si *= betas[j];
+            for (int i = j + 1; i < k; ++i) {
+                yr[i] -= v_r[i] * sr - v_i[i] * si;
+                yi[i] -= v_r[i] * si + v_i[i] * sr;
+            }
+        }
+        for (int i = 0; i < k; ++i) {
+            Vout[2 * ((size_t)c * k + i)] = yr[i];
+            Vout[2 * ((size_t)c * k + i) + 1] = yi[i];
         }
     }
 }
@@ -161,66 +252,95 @@ namespace {
 bool rr_cholesky(int k, const double* GA, const double* GB, const std::vector<double>& dsc, int nwant,
                  double* theta, double* C, int* nout) {
     constexpr double kMinPivot = 1e-4;
-    auto el = [k](const double* G, const std::vector<double>& s, int i, int j) {
-        const size_t o = 2 * ((size_t)j * k + i);
-        return cd(G[o], G[o + 1]) * (s[i] * s[j]);
+    const size_t kk = (size_t)k * k;
+    // L row-major (real and imaginary parts), lower triangle, row by row
+    std::vector<double> Lr(kk, 0.0), Li(kk, 0.0), inv(k);
+    for (int i = 0; i < k; ++i) {
+        const double* ar = &Lr[(size_t)i * k];
+        const double* ai = &Li[(size_t)i * k];
+        for (int j = 0; j <= i; ++j) {
+            const size_t o = 2 * ((size_t)j * k + i);               // GB(i, j), lower triangle as given
+            const double sc = dsc[i] * dsc[j];
+            double sr = GB[o] * sc, si = (i == j) ? 0.0 : GB[o + 1] * sc;
+            double dr, di;                                           // - sum_t L(i,t) conj(L(j,t))
+            dot_conj(j, &Lr[(size_t)j * k], &Li[(size_t)j * k], ar, ai, dr, di);
+            sr -= dr;
+            si -= di;
+            if (i == j) {
+                if (!(sr > kMinPivot)) return false;
+                const double l = std::sqrt(sr);
+                Lr[(size_t)i * k + i] = l;
+                inv[i] = 1.0 / l;
+            } else {
+                Lr[(size_t)i * k + j] = sr * inv[j];
+                Li[(size_t)i * k + j] = si * inv[j];
+            }
+        }
+    }
+    // forward substitution x = L^{-1} b in place on one column (real and imaginary parts)
+    auto lsolve = [&](double* xr, double* xi) {
+        for (int i = 0; i < k; ++i) {
+            const double* ar = &Lr[(size_t)i * k];
+            const double* ai = &Li[(size_t)i * k];
+            double sr, si;
+            dot_plain(i, ar, ai, xr, xi, sr, si);
+            xr[i] = (xr[i] - sr) * inv[i];
+            xi[i] = (xi[i] - si) * inv[i];
+        }
     };
-    std::vector<cd> L((size_t)k * k, cd(0.0));         // column-major lower triangle
-    for (int j = 0; j < k; ++j) {
-        double djj = el(GB, dsc, j, j).real();
-        for (int t = 0; t < j; ++t) djj -= std::norm(L[(size_t)t * k + j]);
-        if (!(djj > kMinPivot)) return false;
-        const double ljj = std::sqrt(djj);
-        L[(size_t)j * k + j] = ljj;
-        for (int i = j + 1; i < k; ++i) {
-            cd sum = el(GB, dsc, i, j);                    // lower triangle as given (i > j)
-            for (int t = 0; t < j; ++t) sum -= L[(size_t)t * k + i] * std::conj(L[(size_t)t * k + j]);
-            L[(size_t)j * k + i] = sum / ljj;
-        }
-    }
-    // X = L^{-1} As (As Hermitian from its lower triangle), column by column
-    std::vector<cd> X((size_t)k * k);
+    // Y = L^{-1} As column by column (As Hermitian from its lower triangle), column-major
+    std::vector<double> Yr(kk), Yi(kk);
     for (int c = 0; c < k; ++c) {
+        double* yr = &Yr[(size_t)c * k];
+        double* yi = &Yi[(size_t)c * k];
         for (int i = 0; i < k; ++i) {
-            cd v = (i >= c) ? el(GA, dsc, i, c) : std::conj(el(GA, dsc, c, i));
-            if (i == c) v = cd(v.real(), 0.0);
-            for (int t = 0; t < i; ++t) v -= L[(size_t)t * k + i] * X[(size_t)c * k + t];
-            X[(size_t)c * k + i] = v / L[(size_t)i * k + i].real();
+            const double sc = dsc[i] * dsc[c];
+            if (i >= c) {
+                const size_t o = 2 * ((size_t)c * k + i);
+                yr[i] = GA[o] * sc;
+                yi[i] = (i == c) ? 0.0 : GA[o + 1] * sc;
+            } else {
+                const size_t o = 2 * ((size_t)i * k + c);
+                yr[i] = GA[o] * sc;
+                yi[i] = -GA[o + 1] * sc;
+            }
         }
+        lsolve(yr, yi);
     }
-    // M = X L^{-H} = (L^{-1} X^H)^H; only the lower triangle is read by herm_eig
-    std::vector<double> M(2 * (size_t)k * k, 0.0);
-    std::vector<cd> col(k);
-    for (int r = 0; r < k; ++r) {                          // column r of L^{-1} X^H
+    // M = L^{-1} Y^H = L^{-1} As L^{-H}; column r from row r of Y, conjugated
+    std::vector<double> M(2 * kk);
+    std::vector<double> wr(k), wi(k);
+    for (int r = 0; r < k; ++r) {
         for (int i = 0; i < k; ++i) {
-            cd v = std::conj(X[(size_t)i * k + r]);
-            for (int t = 0; t < i; ++t) v -= L[(size_t)t * k + i] * col[t];
-            col[i] = v / L[(size_t)i * k + i].real();
+            wr[i] = Yr[(size_t)i * k + r];
+            wi[i] = -Yi[(size_t)i * k + r];
         }
-        for (int i = r; i < k; ++i) {                      // M(i, r) = conj(col[i]) ... row r of the product
-            const cd m = std::conj(col[i]);
-            M[2 * ((size_t)i * k + r)] = m.real();         // entry (r, i): upper; mirror to (i, r)
-            M[2 * ((size_t)i * k + r) + 1] = m.imag();
-            M[2 * ((size_t)r * k + i)] = m.real();
-            M[2 * ((size_t)r * k + i) + 1] = -m.imag();
+        lsolve(wr.data(), wi.data());
+        for (int i = 0; i < k; ++i) {
+            M[2 * ((size_t)r * k + i)] = wr[i];
+            M[2 * ((size_t)r * k + i) + 1] = wi[i];
         }
     }
     const int nv = std::min(nwant, k);
-    std::vector<double> th(k), Y(2 * (size_t)k * k);
-    herm_eig_n(k, M.data(), th.data(), Y.data(), nv);
-    // C = D L^{-H} Y (back substitution with L^H)
-    std::vector<cd> z(k);
+    std::vector<double> th(k), V(2 * (size_t)k * nv);
+    herm_eig_n(k, M.data(), th.data(), V.data(), nv);
+    // C = D L^{-H} V (back substitution with L^H)
     for (int j = 0; j < nv; ++j) {
         theta[j] = th[j];
         for (int i = k - 1; i >= 0; --i) {
-            cd v(Y[2 * ((size_t)j * k + i)], Y[2 * ((size_t)j * k + i) + 1]);
-            for (int t = i + 1; t < k; ++t) v -= std::conj(L[(size_t)i * k + t]) * z[t];
-            z[i] = v / L[(size_t)i * k + i].real();
+            double vr = V[2 * ((size_t)j * k + i)], vi = V[2 * ((size_t)j * k + i) + 1];
+            for (int t = i + 1; t < k; ++t) {                        // - conj(L(t,i)) z_t
+                const double lr = Lr[(size_t)t * k + i], li = Li[(size_t)t * k + i];
+                const double zr = wr[t], zi = wi[t];
+                vr -= lr * zr + li * zi;
+                vi -= lr * zi - li * zr;
+            }
+            wr[i] = vr * inv[i];
+            wi[i] = vi * inv[i];
         }
         for (int i = 0; i < k; ++i) {
-            const cd v = z[i] * dsc[i];
-            C[2 * ((size_t)j * k + i)] = v.real();
-            C[2 * ((size_t)j * k + i) + 1] = v.imag();
+            C[2 * ((size_t)j * k + i)] = wr[i] * dsc[i];
+            C[2 * ((size_t)j * k + i) + 1] = wi[i] * dsc[i];
         }
     }
     *nout = nv;
