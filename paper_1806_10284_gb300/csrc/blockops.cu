@@ -42,6 +42,12 @@ __device__ __forceinline__ void cp_async_c(double2* dst, const double2* src, boo
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
                  : "memory");
 }
+// 16-byte global -> shared copy (both addresses 16-byte aligned); valid = false writes zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -367,6 +373,122 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
             }
         }
     }
+}
+
+// Complex64 combine with the inputs streamed through shared memory.  Same result as
+// k_combine<float2, Co> (out1_j = sum_{i<k} S_i M[i][j], out2_j = sum_{i>=i0} S_i M[i][j],
+// FP32 products and sums) for m <= kStOut outputs.  A block owns kStRows-row tiles
+// (one row per thread, all m outputs in registers) and streams the k input columns
+// in chunks of kStCols through a kStStages-deep ring of cp.async copies, so the
+// loads of later chunks (and of the next tile) are in flight while a chunk is
+// consumed.  Columns are visited in the order i0..k-1, 0..i0-1 with one
+// accumulator: out2 is stored when the first group is complete, out1 at the end.
+constexpr int kStRows = 128, kStCols = 8, kStStages = 4, kStOut = 16;
+
+template <typename Co>
+__global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, size_t ld,
+                                                         const double2* __restrict__ M, int m, int i0,
+                                                         Co* __restrict__ out1, Co* __restrict__ out2) {
+    using Ro = decltype(Co().x);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int k = S.total, tid = threadIdx.x;
+    const int first = i0 < k ? i0 : k;                         // columns i0..k-1 come first
+    const int nchunk = (k + kStCols - 1) / kStCols, kp = nchunk * kStCols;
+    // coefficients [kp][kStOut] in visiting order, zero past k and past m
+    float4* cf = reinterpret_cast<float4*>(smem_raw);
+    float2* stage = reinterpret_cast<float2*>(cf + (size_t)kp * (kStOut / 2));   // [stages][cols][rows]
+    const float2** ps = reinterpret_cast<const float2**>(stage + kStStages * kStCols * kStRows);
+    for (int e = tid; e < kp * kStOut; e += kStRows) {
+        const int pos = e / kStOut, j = e - pos * kStOut;
+        const int i = pos < k - first ? first + pos : pos - (k - first);
+        const double2 v = (j < m && pos < k) ? M[(size_t)j * k + i] : make_double2(0.0, 0.0);
+        reinterpret_cast<float2*>(cf)[e] = make_float2((float)v.x, (float)v.y);
+    }
+    for (int pos = tid; pos < k; pos += kStRows) {
+        const int i = pos < k - first ? first + pos : pos - (k - first);
+        ps[pos] = col_ptr(S, i, ld);
+    }
+    __syncthreads();
+    const size_t ntiles = (ld + kStRows - 1) / kStRows;
+    // out2 is complete after visiting position k - first - 1
+    const int split = k - first - 1, split_chunk = split >= 0 ? split / kStCols : -1;
+    const int split_c = split >= 0 ? split - split_chunk * kStCols : -1;
+    // producer: the next (tile, chunk) stage to request; every call commits one group
+    size_t p_tile = blockIdx.x;
+    int p_chunk = 0, p_buf = 0;
+    auto issue = [&]() {
+        if (p_tile < ntiles) {
+            float2* dst = stage + p_buf * (kStCols * kStRows);
+#pragma unroll
+            for (int q = 0; q < kStCols / 2; ++q) {
+                const int e = tid + kStRows * q;
+                const int c = e / (kStRows / 2), rp = e - c * (kStRows / 2);
+                const int pos = p_chunk * kStCols + c;
+                const size_t row = p_tile * kStRows + 2 * (size_t)rp;
+                const bool ok = pos < k && row < ld;
+                cp_async16(dst + c * kStRows + 2 * rp, ok ? ps[pos] + row : ps[0], ok);
+            }
+        }
+        cp_async_commit();
+        if (++p_chunk == nchunk) {
+            p_chunk = 0;
+            p_tile += gridDim.x;
+        }
+        p_buf = p_buf + 1 == kStStages ? 0 : p_buf + 1;
+    };
+#pragma unroll
+    for (int s = 0; s < kStStages - 1; ++s) issue();
+    int c_buf = 0;
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const size_t row = tile * kStRows + tid;
+        float2 acc[kStOut];
+#pragma unroll
+        for (int j = 0; j < kStOut; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int chunk = 0; chunk < nchunk; ++chunk) {
+            issue();
+            cp_async_wait<kStStages - 1>();
+            __syncthreads();
+            const float2* X = stage + c_buf * (kStCols * kStRows);
+            const float4* w = cf + (size_t)chunk * kStCols * (kStOut / 2);
+            const int store_c = (out2 && chunk == split_chunk) ? split_c : -1;
+#pragma unroll
+            for (int c = 0; c < kStCols; ++c) {
+                const float2 x = X[c * kStRows + tid];
+#pragma unroll
+                for (int q = 0; q < kStOut / 2; ++q) {
+                    const float4 c2 = w[c * (kStOut / 2) + q];
+                    acc[2 * q].x = fmaf(x.x, c2.x, fmaf(-x.y, c2.y, acc[2 * q].x));
+                    acc[2 * q].y = fmaf(x.x, c2.y, fmaf(x.y, c2.x, acc[2 * q].y));
+                    acc[2 * q + 1].x = fmaf(x.x, c2.z, fmaf(-x.y, c2.w, acc[2 * q + 1].x));
+                    acc[2 * q + 1].y = fmaf(x.x, c2.w, fmaf(x.y, c2.z, acc[2 * q + 1].y));
+                }
+                if (c == store_c && row < ld) {
+#pragma unroll
+                    for (int j = 0; j < kStOut; ++j) {
+                        if (j >= m) break;
+                        out2[(size_t)j * ld + row] = mk((Ro)acc[j].x, (Ro)acc[j].y);
+                    }
+                }
+            }
+            c_buf = c_buf + 1 == kStStages ? 0 : c_buf + 1;
+            __syncthreads();
+        }
+        if (row < ld) {
+#pragma unroll
+            for (int j = 0; j < kStOut; ++j) {
+                if (j >= m) break;
+                if (out1) out1[(size_t)j * ld + row] = mk((Ro)acc[j].x, (Ro)acc[j].y);
+                if (out2 && first == k) out2[(size_t)j * ld + row] = mk((Ro)0, (Ro)0);   // empty second sum
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+size_t combine_st_smem(int k) {
+    const int kp = (k + kStCols - 1) / kStCols * kStCols;
+    return (size_t)kp * kStOut * sizeof(float2) + (size_t)kStStages * kStCols * kStRows * sizeof(float2) +
+           (size_t)k * sizeof(void*);
 }
 
 // R_j = AX_j - theta_j X_j;  W_j = tinv .* R_j (tinv indexed by frequency, both coordinates);
@@ -704,9 +826,37 @@ fame_status gram_herm(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V,
     return FAME_OK;
 }
 
+// the staged complex64 combine applies: m <= kStOut, ld even, every column 16-byte aligned
+template <typename C>
+bool combine_st_ok(const BlockList<C>& S, size_t ld, int m) {
+    if (!std::is_same<C, float2>::value || m > kStOut || (ld & 1) || S.total < 1) return false;
+    for (int b = 0; b < BlockList<C>::kMax; ++b)
+        if (S.cols[b] > 0 && (reinterpret_cast<uintptr_t>(S.ptr[b]) & 15)) return false;
+    return true;
+}
+
 template <typename C, typename Co>
 fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2* M, int m, int i0,
                     Co* out1, Co* out2, cudaStream_t st) {
+    if constexpr (std::is_same<C, float2>::value) {
+        if (combine_st_ok(S, ld, m)) {
+            const size_t smem = combine_st_smem(S.total);
+            const void* fn = (const void*)k_combine_st<Co>;
+            fame_status s = kernel_smem(c, fn, smem);
+            if (s != FAME_OK) return s;
+            int per_sm = 0;
+            FAME_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStRows, smem));
+            const size_t ntiles = (ld + kStRows - 1) / kStRows;
+            const unsigned nblk = (unsigned)std::max<size_t>(1, std::min<size_t>((size_t)152 * std::max(per_sm, 1), ntiles));
+            const double outs = (out1 ? m : 0) + (out2 ? m : 0);
+            ProfScope ps(K_COMBINE, false, st, (double)S.total * ld * sizeof(C) + outs * ld * sizeof(Co),
+                         8.0 * S.total * m * (double)ld);
+            k_combine_st<Co><<<nblk, kStRows, smem, st>>>(S, ld, M, m, i0, out1, out2);
+            count_launch();
+            FAME_CUDA_TRY(c, cudaGetLastError());
+            return FAME_OK;
+        }
+    }
     const int MP = ((m + CJ - 1) / CJ) * CJ;
     const size_t smem = (size_t)S.total * MP * sizeof(C) + (size_t)S.total * sizeof(void*);
     fame_status s = kernel_smem(c, (const void*)k_combine<C, Co>, smem);
