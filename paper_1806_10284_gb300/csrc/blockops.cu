@@ -485,6 +485,111 @@ __global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, siz
     cp_async_wait<0>();
 }
 
+// Complex64 Q_j <- Q_j - sum_i X_i c[i][j] (in place, m <= kStOut, nq <= 2 kStOut) with
+// the same cp.async ring as k_combine_st.  A row tile's stream is the Q columns
+// (chunks of kStCols; they initialise the accumulators) followed by the X columns.
+// The block has one 128-thread group per kStOut output columns; every group reads
+// each X chunk, and each group takes only its own Q chunks.
+__global__ void __launch_bounds__(2 * kStRows) k_orth_st(const float2* __restrict__ X, int m, BlockList<float2> Q,
+                                                          size_t ld, const double2* __restrict__ cfs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nq = Q.total, tid = threadIdx.x, nthr = blockDim.x;
+    const int g = tid / kStRows, rl = tid - g * kStRows;
+    float4* cf = reinterpret_cast<float4*>(smem_raw);              // [kStOut][kStOut]: (c[i][2q], c[i][2q+1])
+    float2* stage = reinterpret_cast<float2*>(cf + kStOut * kStOut);
+    float2** qp = reinterpret_cast<float2**>(stage + kStStages * kStCols * kStRows);   // [2 kStOut]
+    for (int e = tid; e < kStOut * 2 * kStOut; e += nthr) {
+        const int i = e / (2 * kStOut), j = e - i * (2 * kStOut);
+        const double2 v = (i < m && j < nq) ? cfs[(size_t)j * m + i] : make_double2(0.0, 0.0);
+        reinterpret_cast<float2*>(cf)[e] = make_float2((float)v.x, (float)v.y);
+    }
+    for (int j = tid; j < 2 * kStOut; j += nthr) qp[j] = j < nq ? const_cast<float2*>(col_ptr(Q, j, ld)) : nullptr;
+    __syncthreads();
+    const int nqc = (nq + kStCols - 1) / kStCols, nxc = (m + kStCols - 1) / kStCols, nchunk = nqc + nxc;
+    const size_t ntiles = (ld + kStRows - 1) / kStRows;
+    size_t p_tile = blockIdx.x;
+    int p_chunk = 0, p_buf = 0;
+    auto issue = [&]() {
+        if (p_tile < ntiles) {
+            float2* dst = stage + p_buf * (kStCols * kStRows);
+            for (int e = tid; e < kStCols * kStRows / 2; e += nthr) {
+                const int c = e / (kStRows / 2), rp = e - c * (kStRows / 2);
+                const size_t row = p_tile * kStRows + 2 * (size_t)rp;
+                const float2* src = nullptr;
+                if (p_chunk < nqc) {
+                    const int j = p_chunk * kStCols + c;
+                    if (j < nq) src = qp[j] + row;
+                } else {
+                    const int i = (p_chunk - nqc) * kStCols + c;
+                    if (i < m) src = X + (size_t)i * ld + row;
+                }
+                const bool ok = src != nullptr && row < ld;
+                cp_async16(dst + c * kStRows + 2 * rp, ok ? src : X, ok);
+            }
+        }
+        cp_async_commit();
+        if (++p_chunk == nchunk) {
+            p_chunk = 0;
+            p_tile += gridDim.x;
+        }
+        p_buf = p_buf + 1 == kStStages ? 0 : p_buf + 1;
+    };
+#pragma unroll
+    for (int s = 0; s < kStStages - 1; ++s) issue();
+    int c_buf = 0;
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const size_t row = tile * kStRows + rl;
+        float2 acc[kStOut];
+#pragma unroll
+        for (int j = 0; j < kStOut; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int ch = 0; ch < nchunk; ++ch) {
+            issue();
+            cp_async_wait<kStStages - 1>();
+            __syncthreads();
+            const float2* B = stage + c_buf * (kStCols * kStRows);
+            if (ch < nqc) {
+                const int lo = ch * kStCols - g * kStOut;            // this group's columns: 0 or kStCols
+                if (lo == 0) {
+#pragma unroll
+                    for (int c = 0; c < kStCols; ++c) acc[c] = B[c * kStRows + rl];
+                } else if (lo == kStCols) {
+#pragma unroll
+                    for (int c = 0; c < kStCols; ++c) acc[kStCols + c] = B[c * kStRows + rl];
+                }
+            } else {
+                const float4* w = cf + (size_t)(ch - nqc) * kStCols * kStOut + g * (kStOut / 2);
+#pragma unroll
+                for (int c = 0; c < kStCols; ++c) {
+                    const float2 x = B[c * kStRows + rl];
+#pragma unroll
+                    for (int q = 0; q < kStOut / 2; ++q) {
+                        const float4 c2 = w[c * kStOut + q];
+                        acc[2 * q].x = fmaf(-x.x, c2.x, fmaf(x.y, c2.y, acc[2 * q].x));
+                        acc[2 * q].y = fmaf(-x.x, c2.y, fmaf(-x.y, c2.x, acc[2 * q].y));
+                        acc[2 * q + 1].x = fmaf(-x.x, c2.z, fmaf(x.y, c2.w, acc[2 * q + 1].x));
+                        acc[2 * q + 1].y = fmaf(-x.x, c2.w, fmaf(-x.y, c2.z, acc[2 * q + 1].y));
+                    }
+                }
+            }
+            c_buf = c_buf + 1 == kStStages ? 0 : c_buf + 1;
+            __syncthreads();
+        }
+        if (row < ld) {
+#pragma unroll
+            for (int j = 0; j < kStOut; ++j) {
+                const int col = g * kStOut + j;
+                if (col < nq) qp[col][row] = acc[j];
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+size_t orth_st_smem() {
+    return (size_t)kStOut * kStOut * sizeof(float4) + (size_t)kStStages * kStCols * kStRows * sizeof(float2) +
+           (size_t)2 * kStOut * sizeof(void*);
+}
+
 size_t combine_st_smem(int k) {
     const int kp = (k + kStCols - 1) / kStCols * kStCols;
     return (size_t)kp * kStOut * sizeof(float2) + (size_t)kStStages * kStCols * kStRows * sizeof(float2) +
@@ -930,6 +1035,27 @@ fame_status orth_against(fame_ctx* c, const CX* X, int m, const BlockList<CQ>& Q
                          const double2* cfs, cudaStream_t st) {
     const int nq = Q.total;
     if (nq == 0) return FAME_OK;
+    if constexpr (std::is_same<CX, float2>::value && std::is_same<CQ, float2>::value) {
+        if (m <= kStOut && nq <= 2 * kStOut && combine_st_ok(Q, ld, 1) &&
+            !(reinterpret_cast<uintptr_t>(X) & 15)) {
+            const size_t smem = orth_st_smem();
+            const void* fn = (const void*)k_orth_st;
+            fame_status s = kernel_smem(c, fn, smem);
+            if (s != FAME_OK) return s;
+            const int threads = nq > kStOut ? 2 * kStRows : kStRows;
+            int per_sm = 0;
+            FAME_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+            const size_t ntiles = (ld + kStRows - 1) / kStRows;
+            const unsigned nblk =
+                (unsigned)std::max<size_t>(1, std::min<size_t>((size_t)152 * std::max(per_sm, 1), ntiles));
+            ProfScope ps(K_ORTH, false, st, (double)ld * (m * sizeof(CX) + 2 * nq * sizeof(CQ)),
+                         8.0 * (double)ld * m * nq);
+            k_orth_st<<<nblk, threads, smem, st>>>(X, m, Q, ld, cfs);
+            count_launch();
+            FAME_CUDA_TRY(c, cudaGetLastError());
+            return FAME_OK;
+        }
+    }
     const int MP = ((nq + CJ - 1) / CJ) * CJ;
     const size_t smem = (size_t)m * MP * sizeof(CX) + (size_t)nq * sizeof(void*);
     fame_status s = kernel_smem(c, (const void*)k_orth<CX, CQ>, smem);
