@@ -16,6 +16,9 @@ namespace {
 // Gram kernel: GT x GT complex outputs per thread, GROWS rows per shared-memory stage
 constexpr int GT = 4;
 constexpr int GROWS = 32;
+// ring-staged complex64 combine / orthogonalisation: rows per tile, columns per
+// stage, stages in flight, outputs per thread group
+constexpr int kStRows = 128, kStCols = 8, kStStages = 4, kStOut = 16;
 
 template <typename C> struct Acc;
 template <> struct Acc<float2> { using T = float; };
@@ -162,6 +165,123 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(BlockList<CU> U, BlockLis
             const int i = ti + TIN * a, j = tj + TJN * b;
             if (i < ku && j < kv) out[(size_t)j * ku + i] = make_double2((double)accr[a][b], (double)acci[a][b]);
         }
+}
+
+// Complex64 Gram partials through a cp.async ring: same outputs and tile ownership
+// as k_gram (FP32 products and sums within a block, partial[blk * nsl + slice]),
+// for blocks that own whole kGRows-row tiles, kGStages tiles in flight.  The block
+// runs nsl slices of the thread tiles; slice s takes the rows t = s (mod nsl) of
+// every staged tile, so one stage feeds all warps with one pair of barriers.
+// Shared memory: per stage, the U and V columns padded to multiples of GT (the
+// padding columns stay zero), each column kGRows + 2 elements long (16-byte
+// aligned, and columns four banks apart).
+constexpr int kGRows = 64, kGStages = 3, kGStride = kGRows + 2;
+
+__global__ void __launch_bounds__(512) k_gram_st(BlockList<float2> U, BlockList<float2> V, size_t ld, int nsl,
+                                                  double2* __restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ku = U.total, kv = V.total, tid = threadIdx.x;
+    const int TIN = (ku + GT - 1) / GT, TJN = (kv + GT - 1) / GT, KU = TIN * GT, KV = TJN * GT;
+    const int ncol = KU + KV, ts = blockDim.x / nsl;
+    float2* ring = reinterpret_cast<float2*>(smem_raw);             // [kGStages][ncol][kGStride]
+    const float2** pc = reinterpret_cast<const float2**>(ring + (size_t)kGStages * ncol * kGStride);
+    for (int c = tid; c < ncol; c += blockDim.x) {
+        const float2* p = nullptr;
+        if (c < ku) p = col_ptr(U, c, ld);
+        else if (c >= KU && c - KU < kv) p = col_ptr(V, c - KU, ld);
+        pc[c] = p;
+    }
+    for (int e = tid; e < kGStages * ncol * kGStride; e += blockDim.x) ring[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int slice = tid / ts, lt = tid - slice * ts;
+    const int ti = lt / TJN, tj = lt - ti * TJN;
+    const bool active = slice < nsl && ti < TIN;
+    const size_t ntiles = (ld + kGRows - 1) / kGRows;
+    size_t p_tile = blockIdx.x;
+    int p_buf = 0;
+    auto issue = [&]() {
+        if (p_tile < ntiles) {
+            float2* dst = ring + (size_t)p_buf * ncol * kGStride;
+            for (int e = tid; e < ncol * (kGRows / 2); e += blockDim.x) {
+                const int c = e / (kGRows / 2), rp = e - c * (kGRows / 2);
+                const float2* col = pc[c];
+                if (!col) continue;                                    // padding column
+                const size_t row = p_tile * kGRows + 2 * (size_t)rp;
+                const bool ok = row < ld;
+                cp_async16(dst + c * kGStride + 2 * rp, ok ? col + row : col, ok);
+            }
+        }
+        cp_async_commit();
+        p_tile += gridDim.x;
+        p_buf = p_buf + 1 == kGStages ? 0 : p_buf + 1;
+    };
+#pragma unroll
+    for (int st = 0; st < kGStages - 1; ++st) issue();
+    float accr[GT][GT], acci[GT][GT];
+#pragma unroll
+    for (int a = 0; a < GT; ++a)
+#pragma unroll
+        for (int b = 0; b < GT; ++b) accr[a][b] = acci[a][b] = 0.f;
+    int c_buf = 0;
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        issue();
+        cp_async_wait<kGStages - 1>();
+        __syncthreads();
+        if (active) {
+            const float2* bu = ring + (size_t)c_buf * ncol * kGStride + (size_t)ti * kGStride;
+            const float2* bv = ring + (size_t)c_buf * ncol * kGStride + (size_t)(KU + tj) * kGStride;
+#pragma unroll 2
+            for (int t = slice; t < kGRows; t += nsl) {
+                float ur[GT], ui[GT], wr[GT], wi[GT];
+#pragma unroll
+                for (int a = 0; a < GT; ++a) {
+                    const float2 x = bu[(size_t)TIN * a * kGStride + t];
+                    ur[a] = x.x;
+                    ui[a] = x.y;
+                }
+#pragma unroll
+                for (int b = 0; b < GT; ++b) {
+                    const float2 x = bv[(size_t)TJN * b * kGStride + t];
+                    wr[b] = x.x;
+                    wi[b] = x.y;
+                }
+#pragma unroll
+                for (int a = 0; a < GT; ++a)
+#pragma unroll
+                    for (int b = 0; b < GT; ++b) {
+                        accr[a][b] = fmaf(ur[a], wr[b], fmaf(ui[a], wi[b], accr[a][b]));
+                        acci[a][b] = fmaf(ur[a], wi[b], fmaf(-ui[a], wr[b], acci[a][b]));
+                    }
+            }
+        }
+        c_buf = c_buf + 1 == kGStages ? 0 : c_buf + 1;
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+    if (!active) return;
+    double2* out = partial + ((size_t)blockIdx.x * nsl + slice) * ku * kv;
+#pragma unroll
+    for (int a = 0; a < GT; ++a)
+#pragma unroll
+        for (int b = 0; b < GT; ++b) {
+            const int i = ti + TIN * a, j = tj + TJN * b;
+            if (i < ku && j < kv) out[(size_t)j * ku + i] = make_double2((double)accr[a][b], (double)acci[a][b]);
+        }
+}
+
+// the ring-staged complex64 kernels apply: m <= kStOut outputs, ld even, every
+// column 16-byte aligned
+template <typename C>
+bool combine_st_ok(const BlockList<C>& S, size_t ld, int m) {
+    if (!std::is_same<C, float2>::value || m > kStOut || (ld & 1) || S.total < 1) return false;
+    for (int b = 0; b < BlockList<C>::kMax; ++b)
+        if (S.cols[b] > 0 && (reinterpret_cast<uintptr_t>(S.ptr[b]) & 15)) return false;
+    return true;
+}
+
+size_t gram_st_smem(int ku, int kv) {
+    const int ncol = ((ku + GT - 1) / GT + (kv + GT - 1) / GT) * GT;
+    return (size_t)kGStages * ncol * kGStride * sizeof(float2) + (size_t)ncol * sizeof(void*);
 }
 
 // Hermitian pair of Gram blocks of LOBPCG: partial[blk] = [U^H U | U^H V] over the
@@ -383,7 +503,6 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
 // loads of later chunks (and of the next tile) are in flight while a chunk is
 // consumed.  Columns are visited in the order i0..k-1, 0..i0-1 with one
 // accumulator: out2 is stored when the first group is complete, out1 at the end.
-constexpr int kStRows = 128, kStCols = 8, kStStages = 4, kStOut = 16;
 
 template <typename Co>
 __global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, size_t ld,
@@ -863,6 +982,36 @@ template <typename CU, typename CV>
 fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, size_t ld,
                  double2* G, cudaStream_t st) {
     const int ku = U.total, kv = V.total;
+    if constexpr (std::is_same<CU, float2>::value && std::is_same<CV, float2>::value) {
+        const int tiles = ((ku + GT - 1) / GT) * ((kv + GT - 1) / GT);
+        const int ts = (tiles + 31) / 32 * 32;
+        const size_t smem = gram_st_smem(ku, kv);
+        if (ts <= 512 && smem <= 200u * 1024u && combine_st_ok(U, ld, 1) && combine_st_ok(V, ld, 1)) {
+            const int nsl = std::min(8, 512 / ts);
+            const void* fn = (const void*)k_gram_st;
+            fame_status s = kernel_smem(c, fn, smem);
+            if (s != FAME_OK) return s;
+            int per_sm = 0;
+            FAME_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, ts * nsl, smem));
+            const size_t ntiles = (ld + kGRows - 1) / kGRows;
+            const int nblk = (int)std::max<size_t>(1, std::min<size_t>((size_t)152 * std::max(per_sm, 1), ntiles));
+            const int nparts = nblk * nsl;
+            if ((s = grow(c, c->partial, (size_t)nparts * ku * kv * sizeof(double2))) != FAME_OK) return s;
+            double2* part = reinterpret_cast<double2*>(c->partial.p);
+            {
+                ProfScope ps(K_GRAM, false, st, (double)ld * (ku + kv) * sizeof(float2), 8.0 * ku * kv * (double)ld);
+                k_gram_st<<<nblk, ts * nsl, smem, st>>>(U, V, ld, nsl, part);
+            }
+            const int kk = ku * kv;
+            {
+                ProfScope ps(K_GRAM_RED, false, st, (double)nparts * kk * sizeof(double2), 2.0 * nparts * kk);
+                k_gram_reduce<<<(kk + 7) / 8, 256, 0, st>>>(part, nparts, kk, G, 0);
+            }
+            count_launch(2);
+            FAME_CUDA_TRY(c, cudaGetLastError());
+            return FAME_OK;
+        }
+    }
     const int tiles = ((ku + GT - 1) / GT) * ((kv + GT - 1) / GT);
     const int groups = (tiles + kGramThreads - 1) / kGramThreads;
     int threads = (((tiles + groups - 1) / groups + 31) / 32) * 32;
@@ -929,15 +1078,6 @@ fame_status gram_herm(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V,
     count_launch(2);
     FAME_CUDA_TRY(c, cudaGetLastError());
     return FAME_OK;
-}
-
-// the staged complex64 combine applies: m <= kStOut, ld even, every column 16-byte aligned
-template <typename C>
-bool combine_st_ok(const BlockList<C>& S, size_t ld, int m) {
-    if (!std::is_same<C, float2>::value || m > kStOut || (ld & 1) || S.total < 1) return false;
-    for (int b = 0; b < BlockList<C>::kMax; ++b)
-        if (S.cols[b] > 0 && (reinterpret_cast<uintptr_t>(S.ptr[b]) & 15)) return false;
-    return true;
 }
 
 template <typename C, typename Co>
