@@ -19,6 +19,7 @@ constexpr int GROWS = 32;
 // ring-staged complex64 combine / orthogonalisation: rows per tile, columns per
 // stage, stages in flight, outputs per thread group
 constexpr int kStRows = 128, kStCols = 8, kStStages = 4, kStOut = 16;
+static_assert(kStOut % kStCols == 0, "a group's outputs span whole stages");
 
 template <typename C> struct Acc;
 template <> struct Acc<float2> { using T = float; };
@@ -269,11 +270,11 @@ __global__ void __launch_bounds__(512) k_gram_st(BlockList<float2> U, BlockList<
         }
 }
 
-// the ring-staged complex64 kernels apply: m <= kStOut outputs, ld even, every
+// the ring-staged complex64 kernels apply: m <= 2 kStOut outputs, ld even, every
 // column 16-byte aligned
 template <typename C>
 bool combine_st_ok(const BlockList<C>& S, size_t ld, int m) {
-    if (!std::is_same<C, float2>::value || m > kStOut || (ld & 1) || S.total < 1) return false;
+    if (!std::is_same<C, float2>::value || m > 2 * kStOut || (ld & 1) || S.total < 1) return false;
     for (int b = 0; b < BlockList<C>::kMax; ++b)
         if (S.cols[b] > 0 && (reinterpret_cast<uintptr_t>(S.ptr[b]) & 15)) return false;
     return true;
@@ -497,33 +498,35 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
 
 // Complex64 combine with the inputs streamed through shared memory.  Same result as
 // k_combine<float2, Co> (out1_j = sum_{i<k} S_i M[i][j], out2_j = sum_{i>=i0} S_i M[i][j],
-// FP32 products and sums) for m <= kStOut outputs.  A block owns kStRows-row tiles
-// (one row per thread, all m outputs in registers) and streams the k input columns
-// in chunks of kStCols through a kStStages-deep ring of cp.async copies, so the
-// loads of later chunks (and of the next tile) are in flight while a chunk is
-// consumed.  Columns are visited in the order i0..k-1, 0..i0-1 with one
-// accumulator: out2 is stored when the first group is complete, out1 at the end.
-
-template <typename Co>
-__global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, size_t ld,
-                                                         const double2* __restrict__ M, int m, int i0,
-                                                         Co* __restrict__ out1, Co* __restrict__ out2) {
+// FP32 products and sums) for m <= 2 kStOut outputs.  A block owns kStRows-row tiles
+// and has one kStRows-thread group per kStOut outputs (one row per thread, the
+// group's outputs in registers); it streams the k input columns in chunks of
+// kStCols through a kStStages-deep ring of cp.async copies, so the loads of later
+// chunks (and of the next tile) are in flight while a chunk is consumed.  Columns
+// are visited in the order i0..k-1, 0..i0-1 with one accumulator: out2 is stored
+// when the first group of columns is complete, out1 at the end.
+template <typename Co, int G>
+__global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(BlockList<float2> S, size_t ld,
+                                                             const double2* __restrict__ M, int m, int i0,
+                                                             Co* __restrict__ out1, Co* __restrict__ out2) {
     using Ro = decltype(Co().x);
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int nthr = G * kStRows, mo = G * kStOut;
     const int k = S.total, tid = threadIdx.x;
+    const int g = tid / kStRows, rl = tid - g * kStRows, j0 = g * kStOut;
     const int first = i0 < k ? i0 : k;                         // columns i0..k-1 come first
     const int nchunk = (k + kStCols - 1) / kStCols, kp = nchunk * kStCols;
-    // coefficients [kp][kStOut] in visiting order, zero past k and past m
+    // coefficients [kp][mo] in visiting order, zero past k and past m
     float4* cf = reinterpret_cast<float4*>(smem_raw);
-    float2* stage = reinterpret_cast<float2*>(cf + (size_t)kp * (kStOut / 2));   // [stages][cols][rows]
+    float2* stage = reinterpret_cast<float2*>(cf + (size_t)kp * (mo / 2));   // [stages][cols][rows]
     const float2** ps = reinterpret_cast<const float2**>(stage + kStStages * kStCols * kStRows);
-    for (int e = tid; e < kp * kStOut; e += kStRows) {
-        const int pos = e / kStOut, j = e - pos * kStOut;
+    for (int e = tid; e < kp * mo; e += nthr) {
+        const int pos = e / mo, j = e - pos * mo;
         const int i = pos < k - first ? first + pos : pos - (k - first);
         const double2 v = (j < m && pos < k) ? M[(size_t)j * k + i] : make_double2(0.0, 0.0);
         reinterpret_cast<float2*>(cf)[e] = make_float2((float)v.x, (float)v.y);
     }
-    for (int pos = tid; pos < k; pos += kStRows) {
+    for (int pos = tid; pos < k; pos += nthr) {
         const int i = pos < k - first ? first + pos : pos - (k - first);
         ps[pos] = col_ptr(S, i, ld);
     }
@@ -538,9 +541,7 @@ __global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, siz
     auto issue = [&]() {
         if (p_tile < ntiles) {
             float2* dst = stage + p_buf * (kStCols * kStRows);
-#pragma unroll
-            for (int q = 0; q < kStCols / 2; ++q) {
-                const int e = tid + kStRows * q;
+            for (int e = tid; e < kStCols * kStRows / 2; e += nthr) {
                 const int c = e / (kStRows / 2), rp = e - c * (kStRows / 2);
                 const int pos = p_chunk * kStCols + c;
                 const size_t row = p_tile * kStRows + 2 * (size_t)rp;
@@ -556,10 +557,10 @@ __global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, siz
         p_buf = p_buf + 1 == kStStages ? 0 : p_buf + 1;
     };
 #pragma unroll
-    for (int s = 0; s < kStStages - 1; ++s) issue();
+    for (int st = 0; st < kStStages - 1; ++st) issue();
     int c_buf = 0;
     for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const size_t row = tile * kStRows + tid;
+        const size_t row = tile * kStRows + rl;
         float2 acc[kStOut];
 #pragma unroll
         for (int j = 0; j < kStOut; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -568,14 +569,14 @@ __global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, siz
             cp_async_wait<kStStages - 1>();
             __syncthreads();
             const float2* X = stage + c_buf * (kStCols * kStRows);
-            const float4* w = cf + (size_t)chunk * kStCols * (kStOut / 2);
+            const float4* w = cf + (size_t)chunk * kStCols * (mo / 2) + g * (kStOut / 2);
             const int store_c = (out2 && chunk == split_chunk) ? split_c : -1;
 #pragma unroll
             for (int c = 0; c < kStCols; ++c) {
-                const float2 x = X[c * kStRows + tid];
+                const float2 x = X[c * kStRows + rl];
 #pragma unroll
                 for (int q = 0; q < kStOut / 2; ++q) {
-                    const float4 c2 = w[c * (kStOut / 2) + q];
+                    const float4 c2 = w[c * (mo / 2) + q];
                     acc[2 * q].x = fmaf(x.x, c2.x, fmaf(-x.y, c2.y, acc[2 * q].x));
                     acc[2 * q].y = fmaf(x.x, c2.y, fmaf(x.y, c2.x, acc[2 * q].y));
                     acc[2 * q + 1].x = fmaf(x.x, c2.z, fmaf(-x.y, c2.w, acc[2 * q + 1].x));
@@ -584,8 +585,8 @@ __global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, siz
                 if (c == store_c && row < ld) {
 #pragma unroll
                     for (int j = 0; j < kStOut; ++j) {
-                        if (j >= m) break;
-                        out2[(size_t)j * ld + row] = mk((Ro)acc[j].x, (Ro)acc[j].y);
+                        if (j0 + j >= m) break;
+                        out2[(size_t)(j0 + j) * ld + row] = mk((Ro)acc[j].x, (Ro)acc[j].y);
                     }
                 }
             }
@@ -595,36 +596,39 @@ __global__ void __launch_bounds__(kStRows) k_combine_st(BlockList<float2> S, siz
         if (row < ld) {
 #pragma unroll
             for (int j = 0; j < kStOut; ++j) {
-                if (j >= m) break;
-                if (out1) out1[(size_t)j * ld + row] = mk((Ro)acc[j].x, (Ro)acc[j].y);
-                if (out2 && first == k) out2[(size_t)j * ld + row] = mk((Ro)0, (Ro)0);   // empty second sum
+                if (j0 + j >= m) break;
+                if (out1) out1[(size_t)(j0 + j) * ld + row] = mk((Ro)acc[j].x, (Ro)acc[j].y);
+                if (out2 && first == k) out2[(size_t)(j0 + j) * ld + row] = mk((Ro)0, (Ro)0);   // empty second sum
             }
         }
     }
     cp_async_wait<0>();
 }
 
-// Complex64 Q_j <- Q_j - sum_i X_i c[i][j] (in place, m <= kStOut, nq <= 2 kStOut) with
+// Complex64 Q_j <- Q_j - sum_i X_i c[i][j] (in place, m <= 2 kStOut, nq <= 4 kStOut) with
 // the same cp.async ring as k_combine_st.  A row tile's stream is the Q columns
 // (chunks of kStCols; they initialise the accumulators) followed by the X columns.
 // The block has one 128-thread group per kStOut output columns; every group reads
 // each X chunk, and each group takes only its own Q chunks.
-__global__ void __launch_bounds__(2 * kStRows) k_orth_st(const float2* __restrict__ X, int m, BlockList<float2> Q,
+template <int G>
+__global__ void __launch_bounds__(G * kStRows) k_orth_st(const float2* __restrict__ X, int m, BlockList<float2> Q,
                                                           size_t ld, const double2* __restrict__ cfs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nq = Q.total, tid = threadIdx.x, nthr = blockDim.x;
+    constexpr int nthr = G * kStRows, nqo = G * kStOut;
+    const int nq = Q.total, tid = threadIdx.x;
     const int g = tid / kStRows, rl = tid - g * kStRows;
-    float4* cf = reinterpret_cast<float4*>(smem_raw);              // [kStOut][kStOut]: (c[i][2q], c[i][2q+1])
-    float2* stage = reinterpret_cast<float2*>(cf + kStOut * kStOut);
-    float2** qp = reinterpret_cast<float2**>(stage + kStStages * kStCols * kStRows);   // [2 kStOut]
-    for (int e = tid; e < kStOut * 2 * kStOut; e += nthr) {
-        const int i = e / (2 * kStOut), j = e - i * (2 * kStOut);
+    const int nqc = (nq + kStCols - 1) / kStCols, nxc = (m + kStCols - 1) / kStCols, nchunk = nqc + nxc;
+    const int mp = nxc * kStCols;
+    float4* cf = reinterpret_cast<float4*>(smem_raw);              // [mp][nqo / 2]: (c[i][2q], c[i][2q+1])
+    float2* stage = reinterpret_cast<float2*>(cf + (size_t)mp * (nqo / 2));
+    float2** qp = reinterpret_cast<float2**>(stage + kStStages * kStCols * kStRows);   // [nqo]
+    for (int e = tid; e < mp * nqo; e += nthr) {
+        const int i = e / nqo, j = e - i * nqo;
         const double2 v = (i < m && j < nq) ? cfs[(size_t)j * m + i] : make_double2(0.0, 0.0);
         reinterpret_cast<float2*>(cf)[e] = make_float2((float)v.x, (float)v.y);
     }
-    for (int j = tid; j < 2 * kStOut; j += nthr) qp[j] = j < nq ? const_cast<float2*>(col_ptr(Q, j, ld)) : nullptr;
+    for (int j = tid; j < nqo; j += nthr) qp[j] = j < nq ? const_cast<float2*>(col_ptr(Q, j, ld)) : nullptr;
     __syncthreads();
-    const int nqc = (nq + kStCols - 1) / kStCols, nxc = (m + kStCols - 1) / kStCols, nchunk = nqc + nxc;
     const size_t ntiles = (ld + kStRows - 1) / kStRows;
     size_t p_tile = blockIdx.x;
     int p_chunk = 0, p_buf = 0;
@@ -667,22 +671,22 @@ __global__ void __launch_bounds__(2 * kStRows) k_orth_st(const float2* __restric
             __syncthreads();
             const float2* B = stage + c_buf * (kStCols * kStRows);
             if (ch < nqc) {
-                const int lo = ch * kStCols - g * kStOut;            // this group's columns: 0 or kStCols
-                if (lo == 0) {
+                const int lo = ch * kStCols - g * kStOut;            // offset in this group's outputs
 #pragma unroll
-                    for (int c = 0; c < kStCols; ++c) acc[c] = B[c * kStRows + rl];
-                } else if (lo == kStCols) {
+                for (int s0 = 0; s0 < kStOut; s0 += kStCols) {
+                    if (lo == s0) {
 #pragma unroll
-                    for (int c = 0; c < kStCols; ++c) acc[kStCols + c] = B[c * kStRows + rl];
+                        for (int c = 0; c < kStCols; ++c) acc[s0 + c] = B[c * kStRows + rl];
+                    }
                 }
             } else {
-                const float4* w = cf + (size_t)(ch - nqc) * kStCols * kStOut + g * (kStOut / 2);
+                const float4* w = cf + (size_t)(ch - nqc) * kStCols * (nqo / 2) + g * (kStOut / 2);
 #pragma unroll
                 for (int c = 0; c < kStCols; ++c) {
                     const float2 x = B[c * kStRows + rl];
 #pragma unroll
                     for (int q = 0; q < kStOut / 2; ++q) {
-                        const float4 c2 = w[c * kStOut + q];
+                        const float4 c2 = w[c * (nqo / 2) + q];
                         acc[2 * q].x = fmaf(-x.x, c2.x, fmaf(x.y, c2.y, acc[2 * q].x));
                         acc[2 * q].y = fmaf(-x.x, c2.y, fmaf(-x.y, c2.x, acc[2 * q].y));
                         acc[2 * q + 1].x = fmaf(-x.x, c2.z, fmaf(x.y, c2.w, acc[2 * q + 1].x));
@@ -704,15 +708,16 @@ __global__ void __launch_bounds__(2 * kStRows) k_orth_st(const float2* __restric
     cp_async_wait<0>();
 }
 
-size_t orth_st_smem() {
-    return (size_t)kStOut * kStOut * sizeof(float4) + (size_t)kStStages * kStCols * kStRows * sizeof(float2) +
-           (size_t)2 * kStOut * sizeof(void*);
+size_t orth_st_smem(int m, int groups) {
+    const int mp = (m + kStCols - 1) / kStCols * kStCols;
+    return (size_t)mp * groups * kStOut * sizeof(float2) +
+           (size_t)kStStages * kStCols * kStRows * sizeof(float2) + (size_t)groups * kStOut * sizeof(void*);
 }
 
-size_t combine_st_smem(int k) {
+size_t combine_st_smem(int k, int groups) {
     const int kp = (k + kStCols - 1) / kStCols * kStCols;
-    return (size_t)kp * kStOut * sizeof(float2) + (size_t)kStStages * kStCols * kStRows * sizeof(float2) +
-           (size_t)k * sizeof(void*);
+    return (size_t)kp * groups * kStOut * sizeof(float2) +
+           (size_t)kStStages * kStCols * kStRows * sizeof(float2) + (size_t)k * sizeof(void*);
 }
 
 // R_j = AX_j - theta_j X_j;  W_j = tinv .* R_j (tinv indexed by frequency, both coordinates);
@@ -1085,18 +1090,22 @@ fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2
                     Co* out1, Co* out2, cudaStream_t st) {
     if constexpr (std::is_same<C, float2>::value) {
         if (combine_st_ok(S, ld, m)) {
-            const size_t smem = combine_st_smem(S.total);
-            const void* fn = (const void*)k_combine_st<Co>;
+            const int groups = (m + kStOut - 1) / kStOut, threads = groups * kStRows;
+            const size_t smem = combine_st_smem(S.total, groups);
+            const void* fn = groups == 1 ? (const void*)k_combine_st<Co, 1> : (const void*)k_combine_st<Co, 2>;
             fame_status s = kernel_smem(c, fn, smem);
             if (s != FAME_OK) return s;
             int per_sm = 0;
-            FAME_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStRows, smem));
+            FAME_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
             const size_t ntiles = (ld + kStRows - 1) / kStRows;
             const unsigned nblk = (unsigned)std::max<size_t>(1, std::min<size_t>((size_t)152 * std::max(per_sm, 1), ntiles));
             const double outs = (out1 ? m : 0) + (out2 ? m : 0);
             ProfScope ps(K_COMBINE, false, st, (double)S.total * ld * sizeof(C) + outs * ld * sizeof(Co),
                          8.0 * S.total * m * (double)ld);
-            k_combine_st<Co><<<nblk, kStRows, smem, st>>>(S, ld, M, m, i0, out1, out2);
+            if (groups == 1)
+                k_combine_st<Co, 1><<<nblk, threads, smem, st>>>(S, ld, M, m, i0, out1, out2);
+            else
+                k_combine_st<Co, 2><<<nblk, threads, smem, st>>>(S, ld, M, m, i0, out1, out2);
             count_launch();
             FAME_CUDA_TRY(c, cudaGetLastError());
             return FAME_OK;
@@ -1176,13 +1185,16 @@ fame_status orth_against(fame_ctx* c, const CX* X, int m, const BlockList<CQ>& Q
     const int nq = Q.total;
     if (nq == 0) return FAME_OK;
     if constexpr (std::is_same<CX, float2>::value && std::is_same<CQ, float2>::value) {
-        if (m <= kStOut && nq <= 2 * kStOut && combine_st_ok(Q, ld, 1) &&
+        if (m <= 2 * kStOut && nq <= 4 * kStOut && combine_st_ok(Q, ld, 1) &&
             !(reinterpret_cast<uintptr_t>(X) & 15)) {
-            const size_t smem = orth_st_smem();
-            const void* fn = (const void*)k_orth_st;
+            const int groups = (nq + kStOut - 1) / kStOut, threads = groups * kStRows;
+            const size_t smem = orth_st_smem(m, groups);
+            const void* fn = groups == 1   ? (const void*)k_orth_st<1>
+                             : groups == 2 ? (const void*)k_orth_st<2>
+                             : groups == 3 ? (const void*)k_orth_st<3>
+                                           : (const void*)k_orth_st<4>;
             fame_status s = kernel_smem(c, fn, smem);
             if (s != FAME_OK) return s;
-            const int threads = nq > kStOut ? 2 * kStRows : kStRows;
             int per_sm = 0;
             FAME_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
             const size_t ntiles = (ld + kStRows - 1) / kStRows;
@@ -1190,7 +1202,12 @@ fame_status orth_against(fame_ctx* c, const CX* X, int m, const BlockList<CQ>& Q
                 (unsigned)std::max<size_t>(1, std::min<size_t>((size_t)152 * std::max(per_sm, 1), ntiles));
             ProfScope ps(K_ORTH, false, st, (double)ld * (m * sizeof(CX) + 2 * nq * sizeof(CQ)),
                          8.0 * (double)ld * m * nq);
-            k_orth_st<<<nblk, threads, smem, st>>>(X, m, Q, ld, cfs);
+            switch (groups) {
+                case 1: k_orth_st<1><<<nblk, threads, smem, st>>>(X, m, Q, ld, cfs); break;
+                case 2: k_orth_st<2><<<nblk, threads, smem, st>>>(X, m, Q, ld, cfs); break;
+                case 3: k_orth_st<3><<<nblk, threads, smem, st>>>(X, m, Q, ld, cfs); break;
+                default: k_orth_st<4><<<nblk, threads, smem, st>>>(X, m, Q, ld, cfs); break;
+            }
             count_launch();
             FAME_CUDA_TRY(c, cudaGetLastError());
             return FAME_OK;

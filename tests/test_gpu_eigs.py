@@ -58,6 +58,19 @@ def test_eigs_small_vs_dense(name, n, flags, rtol):
         assert st["applies_c64"] > 0
 
 
+@pytest.mark.parametrize("nev", [12, 20])
+@pytest.mark.parametrize("flags,rtol", [(fame.FAME_FP64, 1e-10), (fame.FAME_MIXED, 1e-9)])
+def test_eigs_many_bands_vs_dense(nev, flags, rtol):
+    """Blocks wider than 16 vectors (m = 18 and 30): the block kernels run with two
+    output groups (combine) and three or four (orthogonalisation); 2000 rows leave a
+    partial last row tile."""
+    lat, ctx, B = _small("fcc64", (10, 10, 10), seed=9)
+    ref, _ = eigs_dense(lat, 1.0 / B, nev)
+    lam, Y, it = ctx.eigs(nev, tol=1e-10, flags=flags, vectors=True, max_iter=600)
+    np.testing.assert_allclose(lam, ref, rtol=rtol)
+    assert np.all(_residuals(ctx, lam, Y) <= 1e-10 * 1.01)
+
+
 def test_eigs_gamma_excludes_zero_modes():
     lat, ctx, B = _small("fcc64", (6, 6, 6), seed=3, kred=[0.0, 0.0, 0.0])
     ref, _ = eigs_dense(lat, 1.0 / B, 6)
