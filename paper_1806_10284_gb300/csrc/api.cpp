@@ -64,6 +64,20 @@ fame_status grow(fame_ctx* c, GrowBuf& b, size_t bytes) {
     return FAME_OK;
 }
 
+fame_status grow_pinned(fame_ctx* c, GrowBuf& b, size_t bytes) {
+    if (b.bytes >= bytes) return FAME_OK;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaHostAlloc(&b.p, bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, FAME_E_NOMEM, "cudaHostAlloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return FAME_OK;
+}
+
 extern "C" {
 
 const char* fame_version(void) { return "fame-gb300 0.1 (sm_103a)"; }
@@ -306,6 +320,7 @@ void fame_destroy(fame_ctx* c) {
     if (c->solver.p) cudaFree(c->solver.p);
     if (c->solver2.p) cudaFree(c->solver2.p);
     if (c->partial.p) cudaFree(c->partial.p);
+    if (c->pinned.p) cudaFreeHost(c->pinned.p);
     if (c->Y) cudaFree(c->Y);
     delete c;
 }

@@ -146,6 +146,7 @@ struct fame_ctx {
     GrowBuf solver;                // solver blocks
     GrowBuf solver2;               // complex128 blocks of the fallback phase (on demand)
     GrowBuf partial;               // Gram partial sums
+    GrowBuf pinned;                // page-locked host mirror of the solver's small buffers
     fame_solve_stats stats{};
     double stats_rr_ms = 0.0;
     std::string err;
@@ -162,6 +163,7 @@ fame_status set_err(fame_ctx* c, fame_status s, const std::string& msg);
     } while (0)
 
 fame_status grow(fame_ctx* c, GrowBuf& b, size_t bytes);
+fame_status grow_pinned(fame_ctx* c, GrowBuf& b, size_t bytes);   // page-locked host memory
 void count_launch(int k = 1);
 
 // kernel kinds for the opt-in profiler (profile.cpp)

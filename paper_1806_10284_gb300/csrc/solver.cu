@@ -78,12 +78,17 @@ struct Carver {
     }
 };
 
-// Small device/host buffers shared by the phases.
+// Small device buffers shared by the phases, and their page-locked host mirror
+// (read-backs and uploads go through it, so they are direct DMA transfers).
 struct Small {
     double2* G;      // [k][2k]
     double2* Cd;     // [k][m]
     double* theta;   // [m]
     double* part;    // [m][kResidBlocks]
+    double2* hG = nullptr;
+    double2* hC = nullptr;
+    double* htheta = nullptr;
+    double* hpart = nullptr;
 };
 
 size_t small_bytes(int m) {
@@ -115,8 +120,8 @@ struct PhaseOut {
 int host_rr(fame_ctx* c, const Small& sm, int k, int m, int implicit_xx, const std::vector<double>& theta_prev,
             double drop, std::vector<double>& theta, std::vector<double2>& Cm, cudaStream_t st, fame_status* err,
             bool try_cholesky = true) {
-    std::vector<double2> G((size_t)2 * k * k);
-    cudaError_t e = cudaMemcpyAsync(G.data(), sm.G, G.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    const double2* G = sm.hG;
+    cudaError_t e = cudaMemcpyAsync(sm.hG, sm.G, (size_t)2 * k * k * sizeof(double2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         *err = set_err(c, FAME_E_CUDA, std::string("Gram readback: ") + cudaGetErrorString(e));
@@ -124,8 +129,8 @@ int host_rr(fame_ctx* c, const Small& sm, int k, int m, int implicit_xx, const s
     }
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<double> GB(2 * (size_t)k * k), GA(2 * (size_t)k * k);
-    std::memcpy(GB.data(), G.data(), GB.size() * sizeof(double));
-    std::memcpy(GA.data(), G.data() + (size_t)k * k, GA.size() * sizeof(double));
+    std::memcpy(GB.data(), G, GB.size() * sizeof(double));
+    std::memcpy(GA.data(), G + (size_t)k * k, GA.size() * sizeof(double));
     // Hermitise from the lower triangle: entry (i > j) is [W P]^H [AX ...] against the
     // leading X columns, i.e. built from the accurate AX rather than from AW.
     for (int j = 0; j < k; ++j)
@@ -161,8 +166,8 @@ int host_rr_refine(fame_ctx* c, const Small& sm, int m, int nq, const std::vecto
                    double drop, std::vector<double>& theta, std::vector<double2>& Cm, cudaStream_t st,
                    fame_status* err) {
     const size_t cnt = (size_t)nq * (2 * nq + m);
-    std::vector<double2> G(cnt);
-    cudaError_t e = cudaMemcpyAsync(G.data(), sm.G, cnt * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    const double2* G = sm.hG;
+    cudaError_t e = cudaMemcpyAsync(sm.hG, sm.G, cnt * sizeof(double2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         *err = set_err(c, FAME_E_CUDA, std::string("Gram readback: ") + cudaGetErrorString(e));
@@ -210,15 +215,19 @@ int host_rr_refine(fame_ctx* c, const Small& sm, int m, int nq, const std::vecto
 
 fame_status upload_rr(fame_ctx* c, const Small& sm, const std::vector<double2>& Cm,
                       const std::vector<double>& theta, cudaStream_t st) {
-    FAME_CUDA_TRY(c, cudaMemcpyAsync(sm.Cd, Cm.data(), Cm.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-    FAME_CUDA_TRY(c, cudaMemcpyAsync(sm.theta, theta.data(), theta.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    // the previous upload has completed: every upload follows a stream synchronisation
+    std::memcpy(sm.hC, Cm.data(), Cm.size() * sizeof(double2));
+    std::memcpy(sm.htheta, theta.data(), theta.size() * sizeof(double));
+    FAME_CUDA_TRY(c, cudaMemcpyAsync(sm.Cd, sm.hC, Cm.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    FAME_CUDA_TRY(c, cudaMemcpyAsync(sm.theta, sm.htheta, theta.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     return FAME_OK;
 }
 
 fame_status read_norms(fame_ctx* c, const Small& sm, int m, const std::vector<double>& theta,
                        std::vector<double>& res, cudaStream_t st) {
-    std::vector<double> part((size_t)m * kResidBlocks);
-    FAME_CUDA_TRY(c, cudaMemcpyAsync(part.data(), sm.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    const double* part = sm.hpart;
+    FAME_CUDA_TRY(c, cudaMemcpyAsync(sm.hpart, sm.part, (size_t)m * kResidBlocks * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st));
     FAME_CUDA_TRY(c, cudaStreamSynchronize(st));
     res.assign(m, 0.0);
     for (int j = 0; j < m; ++j) {
@@ -472,7 +481,16 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
         bytes += 4 * (((size_t)k * ld * sizeof(double2) + 255));
     if ((s = grow(c, c->solver, bytes)) != FAME_OK) return s;
     Carver cv(c->solver.p);
-    const Small sm = carve_small(cv, m);
+    Small sm = carve_small(cv, m);
+    {
+        if ((s = grow_pinned(c, c->pinned, small_bytes(m) + 256)) != FAME_OK) return s;
+        Carver hcv(c->pinned.p);
+        const Small h = carve_small(hcv, m);
+        sm.hG = h.G;
+        sm.hC = h.Cd;
+        sm.htheta = h.theta;
+        sm.hpart = h.part;
+    }
     const uint64_t seed = 0x5eedF00Dull ^ ((uint64_t)c->n << 20) ^ (uint64_t)nev;
     const bool warm = (flags & FAME_WARM_START) && c->Y && c->Y_nev >= 1;
     const int nwarm = warm ? std::min(c->Y_nev, m) : 0;
