@@ -44,7 +44,8 @@ def _residuals(ctx, lam, Y):
 
 
 @pytest.mark.parametrize("name,n", [("fcc64", (6, 6, 6)), ("tri192", (8, 6, 5)),
-                                    ("hex96", (8, 8, 5)), ("bcc96", (6, 6, 6))])
+                                    ("hex96", (8, 8, 5)), ("bcc96", (6, 6, 6)),
+                                    ("sc16", (4, 4, 3))])   # 96 rows: less than one row tile
 @pytest.mark.parametrize("flags,rtol", [(fame.FAME_FP64, 1e-10), (fame.FAME_MIXED, 1e-9)])
 def test_eigs_small_vs_dense(name, n, flags, rtol):
     lat, ctx, B = _small(name, n, seed=7)
