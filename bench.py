@@ -15,7 +15,9 @@ After the timed steps (outside the timed region) a single-GPU run also reports
 the plain FP64 solve of the same problem (``fp64_time_to_10_bands_s``) and a
 band-path batch on the BCC, hexagonal and monoclinic workloads solved one
 problem after another and as one concurrent ``fame_eigs_batched`` call
-(``band_path``); ``--no-extras`` skips both.
+(``band_path``); ``--no-extras`` skips both.  ``--band-path-k K`` adds the full band
+paths (K Bloch vectors per lattice, one batched mixed call per lattice, and a
+plain FP64 solve of three of them per lattice) as ``band_paths``.
 
 Under torchrun each rank solves its own Bloch vector (independent problems,
 no data-path collective: weak scaling).  ``--impl reference`` times the CPU
@@ -59,6 +61,10 @@ def parse():
                          "runs, where the profiler's overhead would skew the tuning)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-FP64 solve and the band-path batch after the timed steps")
+    ap.add_argument("--band-path-k", type=int, default=0, metavar="K",
+                    help="after the timed steps, also solve the full band paths: K Bloch vectors per "
+                         "lattice (K <= 60) in one batched mixed call per lattice, plus a plain FP64 "
+                         "solve of three of them per lattice (several minutes for K = 60)")
     return ap.parse_args()
 
 
@@ -295,6 +301,47 @@ def comparisons(ctx, lam_mixed, k_per_lattice=2):
     return res
 
 
+def band_paths(k_per_lattice):
+    """The band paths in full: per lattice, k_per_lattice Bloch vectors of its path solved
+    in one batched mixed call, and three of them again by the plain FP64 solver."""
+    import torch
+    from paper_1806_10284_gb300 import fame
+    from paper_1806_10284_gb300 import workloads as W
+    out = {}
+    for name in BAND_PATH:
+        w = W.WORKLOADS[name]
+        Ks = W.bloch_vectors(name)
+        idx = np.linspace(0, len(Ks) - 1, min(k_per_lattice, len(Ks))).astype(int)
+        ctxs, eps = [], None
+        for i in idx:
+            c = fame.Context(w["vectors"], w["n"], Ks[i])
+            if eps is None:
+                eps = W.eps_for(name, c.geometry())
+            c.set_eps(*eps)
+            ctxs.append(c)
+        ctxs[0].eigs(NEV, tol=TOL, flags=fame.FAME_MIXED)          # first-use allocations
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lam_b, its = fame.eigs_batched(ctxs, NEV, tol=TOL, flags=fame.FAME_MIXED, max_iter=600)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        t64, rel = [], []
+        for j in sorted(set([min(1, len(ctxs) - 1), len(ctxs) // 2, max(0, len(ctxs) - 2)])):
+            t0 = time.perf_counter()
+            l64 = ctxs[j].eigs(NEV, tol=TOL, flags=fame.FAME_FP64, max_iter=800)[0]
+            torch.cuda.synchronize()
+            t64.append(time.perf_counter() - t0)
+            rel.append(float(np.max(np.abs(lam_b[j] - l64) / np.abs(l64))))
+        out[name] = {"grid": list(w["n"]), "k_points": len(ctxs), "batched_mixed_s": t_b,
+                     "batched_per_k_s": t_b / len(ctxs), "iterations_min_max": [int(min(its)), int(max(its))],
+                     "fp64_per_k_s": t64, "fp64_for_all_k_estimate_s": float(np.mean(t64)) * len(ctxs),
+                     "batched_vs_fp64_max_rel": max(rel)}
+        for c in ctxs:
+            c.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # the two arms
 # ---------------------------------------------------------------------------
@@ -435,6 +482,8 @@ def run_ours(args, rank, world, local):
     extras = None
     if world == 1 and not args.no_extras:
         extras = comparisons(ctx, lam)
+    if world == 1 and args.band_path_k > 0:
+        extras = dict(extras or {}, band_paths=band_paths(args.band_path_k))
     if rank != 0:
         return
     rl = roofline(prof)
