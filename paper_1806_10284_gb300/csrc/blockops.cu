@@ -962,30 +962,6 @@ __global__ void k_random(C* __restrict__ X, size_t N, uint64_t seed) {
     }
 }
 
-// start block: X <- scale X, then X[j][idx[j]] += 1 for the listed coordinates
-constexpr int kSpikes = 64;
-struct SpikeList {
-    long long idx[kSpikes];
-    int count;
-};
-
-template <typename C>
-__global__ void k_scale(C* __restrict__ X, size_t N, double scale) {
-    using R = decltype(X[0].x);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
-         i += (size_t)gridDim.x * blockDim.x)
-        X[i] = mk((R)(X[i].x * scale), (R)(X[i].y * scale));
-}
-
-template <typename C>
-__global__ void k_spikes(C* __restrict__ X, size_t ld, SpikeList sp) {
-    const int j = threadIdx.x;
-    if (j < sp.count) {
-        C& v = X[(size_t)j * ld + (size_t)sp.idx[j]];
-        v.x += 1;
-    }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1277,23 +1253,6 @@ fame_status random_block(fame_ctx* c, C* X, int m, uint64_t seed, const typename
 }
 
 template <typename C>
-fame_status seed_block(fame_ctx* c, C* X, int m, const std::vector<long long>& coords, double scale,
-                       cudaStream_t st) {
-    const size_t ld = 2 * (size_t)c->n;
-    SpikeList sp{};
-    sp.count = (int)std::min<size_t>({coords.size(), (size_t)m, (size_t)kSpikes});
-    for (int j = 0; j < sp.count; ++j) {
-        if (coords[j] < 0 || (size_t)coords[j] >= ld) return set_err(c, FAME_E_ARG, "seed_block: coordinate out of range");
-        sp.idx[j] = coords[j];
-    }
-    k_scale<C><<<152 * 8, 256, 0, st>>>(X, (size_t)m * ld, scale);
-    k_spikes<C><<<1, kSpikes, 0, st>>>(X, ld, sp);
-    count_launch(2);
-    FAME_CUDA_TRY(c, cudaGetLastError());
-    return FAME_OK;
-}
-
-template <typename C>
 fame_status mask_block(fame_ctx* c, C* X, int m, const typename RealOf<C>::T* tinv, cudaStream_t st) {
     k_mask<C><<<152 * 8, 256, 0, st>>>(X, tinv, (size_t)c->n, m);
     count_launch();
@@ -1315,6 +1274,4 @@ template fame_status convert<double2, float2>(fame_ctx*, const double2*, float2*
 template fame_status random_block<float2>(fame_ctx*, float2*, int, uint64_t, const float*, cudaStream_t);
 template fame_status random_block<double2>(fame_ctx*, double2*, int, uint64_t, const double*, cudaStream_t);
 template fame_status mask_block<float2>(fame_ctx*, float2*, int, const float*, cudaStream_t);
-template fame_status seed_block<float2>(fame_ctx*, float2*, int, const std::vector<long long>&, double, cudaStream_t);
-template fame_status seed_block<double2>(fame_ctx*, double2*, int, const std::vector<long long>&, double, cudaStream_t);
 template fame_status mask_block<double2>(fame_ctx*, double2*, int, const double*, cudaStream_t);

@@ -81,7 +81,3 @@ fame_status random_block(fame_ctx* c, C* X, int m, uint64_t seed,
 template <typename C>
 fame_status mask_block(fame_ctx* c, C* X, int m, const typename RealOf<C>::T* tinv,
                        cudaStream_t st);
-// X <- scale X, then column j gets +1 at row coords[j] (j < min(m, 64, coords.size()))
-template <typename C>
-fame_status seed_block(fame_ctx* c, C* X, int m, const std::vector<long long>& coords, double scale,
-                       cudaStream_t st);

@@ -28,7 +28,6 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
-#include <numeric>
 #include <thread>
 #include <utility>
 #include <vector>
@@ -235,31 +234,6 @@ fame_status read_norms(fame_ctx* c, const Small& sm, int m, const std::vector<do
         double ss = 0.0;
         for (int b = 0; b < kResidBlocks; ++b) ss += part[(size_t)j * kResidBlocks + b];
         res[j] = std::sqrt(ss) / std::fabs(theta[j]);
-    }
-    return FAME_OK;
-}
-
-// Start block of the eigensolver: the m range coordinates of smallest Lambda_q
-// (largest preconditioner entry; both coordinates of a frequency together, ties by
-// index) are the exact eigenvectors for homogeneous eps, so each column starts at
-// one of them, plus a random part of 0.3 of its norm that keeps every direction
-// present.  Returns the coordinates (row offsets in a [2][n] column).
-fame_status low_lambda_coords(fame_ctx* c, int m, cudaStream_t st, std::vector<long long>& coords) {
-    const size_t n = (size_t)c->n;
-    std::vector<float> t(n);
-    FAME_CUDA_TRY(c, cudaMemcpyAsync(t.data(), c->tf.tinv, n * sizeof(float), cudaMemcpyDeviceToHost, st));
-    FAME_CUDA_TRY(c, cudaStreamSynchronize(st));
-    const size_t nf = std::min(n, (size_t)(m + 1) / 2);
-    std::vector<long long> f(n);
-    std::iota(f.begin(), f.end(), 0LL);
-    std::partial_sort(f.begin(), f.begin() + nf, f.end(), [&](long long a, long long b) {
-        return t[a] > t[b] || (t[a] == t[b] && a < b);
-    });
-    coords.clear();
-    for (size_t i = 0; i < nf && (int)coords.size() < m; ++i) {
-        if (!(t[f[i]] > 0.0f)) break;                        // Gamma null coordinates stay empty
-        coords.push_back(f[i]);
-        if ((int)coords.size() < m) coords.push_back((long long)n + f[i]);
     }
     return FAME_OK;
 }
@@ -518,10 +492,6 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
         sm.hpart = h.part;
     }
     const uint64_t seed = 0x5eedF00Dull ^ ((uint64_t)c->n << 20) ^ (uint64_t)nev;
-    // random entries are uniform in [-1/2, 1/2]^2, so a column has norm about sqrt(n / 3)
-    std::vector<long long> coords;
-    if ((s = low_lambda_coords(c, m, st, coords)) != FAME_OK) return s;
-    const double start_scale = 0.3 / std::sqrt((double)n / 3.0);
     const bool warm = (flags & FAME_WARM_START) && c->Y && c->Y_nev >= 1;
     const int nwarm = warm ? std::min(c->Y_nev, m) : 0;
     PhaseOut ph1, ph2;
@@ -535,7 +505,6 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
         for (int i = 0; i < 2; ++i) { X64[i] = cv.take<double2>((size_t)m * ld); AX64[i] = cv.take<double2>((size_t)m * ld); }
         float2* R32 = cv.take<float2>((size_t)m * ld);
         if ((s = random_block<float2>(c, S[0], m, seed, c->tf.tinv, st)) != FAME_OK) return s;
-        if ((s = seed_block<float2>(c, S[0], m, coords, start_scale, st)) != FAME_OK) return s;
         if (warm && (s = convert<double2, float2>(c, reinterpret_cast<const double2*>(c->Y), S[0], (size_t)nwarm * ld, st)) != FAME_OK) return s;
         const double tol32 = std::max(tol, 2e-5);
         if ((s = lob_explicit<float2>(c, S, AS, sm, m, nev, tol32, max_iter, true, 1e-6, st, ph1)) != FAME_OK) return s;
@@ -567,7 +536,6 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
         double2* AS[2];
         for (int i = 0; i < 2; ++i) { S[i] = cv.take<double2>((size_t)k * ld); AS[i] = cv.take<double2>((size_t)k * ld); }
         if ((s = random_block<double2>(c, S[0], m, seed, c->td.tinv, st)) != FAME_OK) return s;
-        if ((s = seed_block<double2>(c, S[0], m, coords, start_scale, st)) != FAME_OK) return s;
         if (warm) FAME_CUDA_TRY(c, cudaMemcpyAsync(S[0], c->Y, (size_t)nwarm * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
         if ((s = lob_explicit<double2>(c, S, AS, sm, m, nev, tol, max_iter, false, 1e-12, st, ph2)) != FAME_OK) return s;
         c->stats.iters_fp64 = ph2.iters;
