@@ -86,25 +86,89 @@ def workload_inputs(rank):
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (the reference arm and the cpu_baseline field)
 # ---------------------------------------------------------------------------
-def oracle_apply_rate(seconds, rank=0, min_vectors=2):
-    """Oracle FP64 A_r applies/s on random vectors of the workload (single process)."""
+def _oracle_inputs(rank=0):
+    """Lattice arguments and 1/B of this rank's problem, for the oracle workers."""
     from oracle.lattice import make_lattice
-    from oracle.nfsep import apply_Ar, bases
     from paper_1806_10284_gb300 import workloads as W
     vec, n, K = workload_inputs(rank)
     lat = make_lattice(vec, n, K)
     geom = W.Geometry(n=n, s=(lat.s1, lat.s2, lat.s3), delta=(lat.dx, lat.dy, lat.dz), perm=lat.perm)
-    B = W.eps_for(WORKLOAD, geom)
-    invB = np.stack([1.0 / b for b in B])
+    invB = np.stack([1.0 / b for b in W.eps_for(WORKLOAD, geom)])
+    return vec, n, K, invB
+
+
+def _oracle_worker(args, tasks, results):
+    """One host core: build the oracle's lattice and range basis once, then serve tasks:
+    ("time", s) applies A_r (FP64) to a vector until s seconds have passed (at least once),
+    ("count", k) applies it k times; each answers (applies, seconds).  None ends it."""
+    vec, n, K, invB, seed = args
+    from oracle.lattice import make_lattice
+    from oracle.nfsep import apply_Ar, bases
+    lat = make_lattice(vec, n, K)
     b = bases(lat)
-    rng = np.random.default_rng(0)
-    done, t0 = 0, time.perf_counter()
-    while done < min_vectors or time.perf_counter() - t0 < seconds:
-        y = rng.standard_normal((2,) + lat.shape) + 1j * rng.standard_normal((2,) + lat.shape)
-        apply_Ar(lat, y, invB, b)
-        done += 1
-    dt = time.perf_counter() - t0
-    return done / dt, done, dt
+    rng = np.random.default_rng(seed)
+    y = rng.standard_normal((2,) + lat.shape) + 1j * rng.standard_normal((2,) + lat.shape)
+    results.put(("ready", 0.0))
+    while True:
+        task = tasks.get()
+        if task is None:
+            return
+        kind, amount = task
+        done, t0 = 0, time.perf_counter()
+        while (done < 1 or time.perf_counter() - t0 < amount) if kind == "time" else done < amount:
+            apply_Ar(lat, y, invB, b)
+            done += 1
+        results.put((done, time.perf_counter() - t0))
+
+
+class OraclePool:
+    """The CPU oracle on every host core: one spawned process per core (one numpy thread
+    each), every process applying A_r to its own vector of the workload."""
+
+    def __init__(self, rank=0, workers=None):
+        import multiprocessing as mp
+        self.workers = workers or os.cpu_count() or 1
+        vec, n, K, invB = _oracle_inputs(rank)
+        mpc = mp.get_context("spawn")
+        self.tasks, self.results = mpc.Queue(), mpc.Queue()
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.procs = [mpc.Process(target=_oracle_worker, daemon=True,
+                                      args=((vec, n, K, invB, 1000 + i), self.tasks, self.results))
+                          for i in range(self.workers)]
+            for pr in self.procs:
+                pr.start()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        for _ in self.procs:
+            self.results.get(timeout=900)
+
+    def _run(self, task):
+        t0 = time.perf_counter()
+        for _ in self.procs:
+            self.tasks.put(task)
+        out = [self.results.get(timeout=900) for _ in self.procs]
+        return sum(d for d, _ in out), time.perf_counter() - t0
+
+    def timed(self, seconds):
+        """(applies, wall seconds) with every process applying for about ``seconds``."""
+        return self._run(("time", seconds))
+
+    def one_each(self):
+        """(applies, wall seconds) of one apply per process."""
+        return self._run(("count", 1))
+
+    def close(self):
+        for _ in self.procs:
+            self.tasks.put(None)
+        for pr in self.procs:
+            pr.join(timeout=60)
 
 
 # ---------------------------------------------------------------------------
@@ -206,19 +270,25 @@ def traffic_for(kernel):
     return None if k is None else k.get("dram_bytes_per_launch")
 
 
-def _bound(name):
-    """(bound, peak, unit, peak source) of a profiler kernel kind."""
+def _bound(name, st):
+    """(bound, peak, unit, peak source) of a profiler kernel kind.  The complex64 FFT
+    passes are HBM bound (the pass model); every other kernel is HBM bound when its
+    algorithmic intensity (flops per algorithmic byte) lies below the ridge of the
+    arithmetic units it runs on (FP32 lanes for complex64 work and for the double-float
+    update, FP64 units for complex128 work), else bound by those units."""
     base, prec = name.rsplit("_", 1)
+    hbm, kind = measured_peaks()
+    hbm_src = (f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else "fallback 6.8 TB/s")
     if base in FFT_PASSES and prec == "c64":
-        hbm, kind = measured_peaks()
-        return "hbm", hbm, "GB/s", (f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured"
-                                    else "fallback 6.8 TB/s")
-    if base == "combine_df":
-        return "alu", FP32_PEAK_TFLOPS, "TFLOP/s", ("FP32 lanes x clock (recipe table: 152 SMs, 2.07 GHz); "
-                                                    "double-float sums on FP32 units, flops = FP32 operations")
-    if prec == "c128":
-        return "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "nominal FP64 rate (recipe table)"
-    return "alu", FP32_PEAK_TFLOPS, "TFLOP/s", "FP32 lanes x clock (recipe table: 152 SMs, 2.07 GHz)"
+        return "hbm", hbm, "GB/s", hbm_src
+    if prec == "c128" and base != "combine_df":
+        alu, alu_src = FP64_PEAK_TFLOPS, "nominal FP64 rate (recipe table)"
+    else:
+        alu, alu_src = FP32_PEAK_TFLOPS, "FP32 lanes x clock (recipe table: 152 SMs, 2.07 GHz)"
+    intensity = st["flops"] / max(st["bytes"], 1.0)
+    if intensity < alu * 1e12 / (hbm * 1e9):
+        return "hbm", hbm, "GB/s", hbm_src
+    return "alu", alu, "TFLOP/s", alu_src
 
 
 def roofline(prof):
@@ -227,13 +297,14 @@ def roofline(prof):
         return None
     name, st = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
     secs = st["total_ms"] / 1e3
-    bound, peak, unit, src = _bound(name)
+    bound, peak, unit, src = _bound(name, st)
     ach = st["bytes"] / secs / 1e9 if bound == "hbm" else st["flops"] / secs / 1e12
     return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
             "frac": ach / peak, "traffic": traffic_for(name), "peak_source": src,
             "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"],
             "bytes_per_launch": st["bytes"] / st["launches"],
             "flops_per_launch": st["flops"] / st["launches"],
+            "intensity_flop_per_byte": st["flops"] / max(st["bytes"], 1.0),
             "share_of_kernel_time": st["total_ms"] / sum(v["total_ms"] for v in prof.values())}
 
 
@@ -348,15 +419,17 @@ def band_paths(k_per_lattice):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    sample = 4
+    pool = OraclePool()
+    cores = pool.workers
     for _ in range(args.warmup):
-        oracle_apply_rate(0.0, min_vectors=1)
+        pool.one_each()
     t = 0.0
     done = 0
     for _ in range(args.steps):
-        rate, d, dt = oracle_apply_rate(0.0, min_vectors=sample)
+        d, dt = pool.one_each()
         t += dt
         done += d
+    pool.close()
     value = done / t
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -364,10 +437,10 @@ def run_reference(args, rank, world):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "fcc64: FCC primitive (a/2)(0,1,1),(a/2)(1,0,1),(a/2)(1,1,0), 64^3, "
                                   "eps=13 diamond-site spheres, A_r applies (oracle: FP64 numpy)",
-                      "sample_per_step": f"{sample} single-vector A_r applies"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{args.steps} steps x {sample} FP64 applies at FCC 64^3, "
-                                      "single process (numpy FFT)"},
+                      "sample_per_step": f"one single-vector A_r apply on each of {cores} host cores"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} steps x {cores} FP64 applies at FCC 64^3, one "
+                                      "process per host core (numpy FFT, one thread each)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -376,11 +449,14 @@ def run_ours(args, rank, world, local):
     import torch
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # before any GPU work: oracle FP64 applies on host cores, bounded sample
-        rate, done, dt = oracle_apply_rate(args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{done} FP64 single-vector A_r applies at FCC 64^3 in {dt:.1f} s "
-                         "(numpy FFT, one process)"}
+        # before any GPU work: oracle FP64 applies on every host core, bounded sample
+        pool = OraclePool()
+        done, dt = pool.timed(args.cpu_seconds)
+        cores = pool.workers
+        pool.close()
+        cpu = {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{done} FP64 single-vector A_r applies at FCC 64^3 in {dt:.1f} s, one "
+                         f"process per host core ({cores}; numpy FFT, one thread each)"}
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -421,7 +497,6 @@ def run_ours(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)
-    fame.profile(True)
     launches0 = fame.launch_count()
     total_ms = 0.0
     eig_ms = 0.0
@@ -442,9 +517,23 @@ def run_ours(args, rank, world, local):
         applies64 += st["applies_c128"]
         resid = max(resid, st["max_residual"])
     launches = fame.launch_count() - launches0
+    clk = clocks.stop()
+    # the per-kernel table and the roofline: the same steps again with every launch
+    # bracketed by CUDA events on its stream (kept out of the timed steps above, whose
+    # value carries no per-launch event work)
+    fame.profile(True)
+    prof_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        prof_ms += e0.elapsed_time(e1)
     fame.profile(False)
     prof = fame.profile_read()
-    clk = clocks.stop()
     # max over ranks of the timed region, sum of work
     if world > 1:
         import torch.distributed as dist
@@ -508,6 +597,7 @@ def run_ours(args, rank, world, local):
            "complex128_applies_per_step": applies64 / args.steps,
            "gpu_launches": launches,
            "clocks": clk,
+           "profiled_ms_per_step": prof_ms / args.steps,
            "roofline": rl,
            "apply_roofline": apply_roofline(prof),
            "apply_plan_c64": plan,

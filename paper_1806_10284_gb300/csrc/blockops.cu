@@ -1165,13 +1165,13 @@ fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<
     fame_status s = kernel_smem(c, (const void*)k_combine_mixed, smem);
     if (s != FAME_OK) return s;
     {
-        // FP32 operations of the double-float algorithm: per complex X coefficient four
-        // double-float products (one multiply, three FMAs, a six-operation two-sum and two
-        // adds: 15 flops counting an FMA as two), plus complex64 MACs (8 flops) for Q
+        // algorithmic work: 8 flops per complex multiply-add, for the X and the Q part
+        // alike (the double-float arithmetic of the X part spends about 60 FP32
+        // operations per complex coefficient, which is how it is computed, not how much)
         ProfScope ps(K_COMBINE_DF, true, st,
                      (double)ld * (m * sizeof(double2) + nq * sizeof(float2) +
                                    m * (sizeof(double2) + (X32n ? sizeof(float2) : 0) + (Pn ? sizeof(float2) : 0))),
-                     (double)ld * m * (4.0 * 15.0 * m + 8.0 * nq));
+                     (double)ld * m * (8.0 * m + 8.0 * nq));
         k_combine_mixed<<<152 * 8, 256, smem, st>>>(X, m, Q, ld, M, Xn, X32n, Pn);
     }
     count_launch();

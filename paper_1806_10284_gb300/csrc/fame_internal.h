@@ -236,8 +236,13 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
 // pairs.  drop: relative threshold on the scaled GB spectrum below which
 // directions are discarded.  try_cholesky: reduce through the Cholesky factor of
 // GB when it is well conditioned (else, and when false, through its
-// eigen-decomposition).  Returns the number of pairs produced.
+// eigen-decomposition).  Returns the number of pairs produced, or kRRNoConv if an
+// implicit QR ran out of sweeps (the outputs are then not eigenpairs).
+constexpr int kRRNoConv = -2;
 int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double drop,
                   double* theta, double* C, bool try_cholesky = true);
 // Hermitian eigensolver (ascending), A column-major k x k complex; V may alias nothing.
-void herm_eig(int k, const double* A, double* w, double* V);
+// false if the implicit QR did not converge within its sweep limit.
+bool herm_eig(int k, const double* A, double* w, double* V);
+// total sweep limit of the implicit QR (0: the default of 60 per matrix order; for tests)
+void rr_set_qr_sweep_limit(int total);

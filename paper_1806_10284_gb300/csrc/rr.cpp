@@ -19,6 +19,12 @@
 
 using cd = std::complex<double>;
 
+// Sweep limit of the implicit QR: 60 per matrix order by default (each eigenvalue
+// deflates after a few sweeps, so this is far more than convergence takes); a
+// positive value set for tests replaces it by that total.
+static int g_qr_sweep_total = 0;
+void rr_set_qr_sweep_limit(int total) { g_qr_sweep_total = total > 0 ? total : 0; }
+
 namespace {
 
 // sum_i conj(a_i) b_i and sum_i a_i b_i over split complex vectors, with four
@@ -68,13 +74,16 @@ inline void dot_plain(int n, const double* ar, const double* ai, const double* b
 
 // implicit symmetric QR on the tridiagonal (d, e) with the Wilkinson shift from the
 // trailing 2 x 2 block, deflation where |e_i| <= eps (|d_i| + |d_i+1|); the
-// rotations are accumulated into Z
-void tridiag_qr(int k, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
+// rotations are accumulated into Z.  Returns false if the sweep limit ran out
+// before every off-diagonal entry was deflated.
+bool tridiag_qr(int k, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
     // d[0..k-1] diagonal, e[0..k-2] off-diagonal; Z (k x k, column-major) accumulates rotations
     const double eps = 2.220446049250313e-16;
     int hi = k - 1;
     int guard = 0;
-    while (hi > 0 && guard < 60 * k) {
+    const int limit = g_qr_sweep_total > 0 ? g_qr_sweep_total : 60 * k;
+    while (hi > 0) {
+        if (guard >= limit) return false;
         if (std::fabs(e[hi - 1]) <= eps * (std::fabs(d[hi - 1]) + std::fabs(d[hi]))) {
             e[hi - 1] = 0.0;
             --hi;
@@ -112,16 +121,18 @@ void tridiag_qr(int k, std::vector<double>& d, std::vector<double>& e, std::vect
             }
         }
     }
+    return true;
 }
 
 }  // namespace
 
-void herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec);
+bool herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec);
 
-void herm_eig(int k, const double* Ain, double* w, double* Vout) { herm_eig_n(k, Ain, w, Vout, k); }
+bool herm_eig(int k, const double* Ain, double* w, double* Vout) { return herm_eig_n(k, Ain, w, Vout, k); }
 
-// as herm_eig, eigenvectors of the nvec smallest eigenvalues only (all k eigenvalues)
-void herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec) {
+// as herm_eig, eigenvectors of the nvec smallest eigenvalues only (all k eigenvalues);
+// false if the tridiagonal QR did not converge (the outputs are then not eigenpairs)
+bool herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec) {
     // real and imaginary parts, column-major, lower triangle used; the reflector
     // H_j = I - beta_j v_j v_j^H maps column j below the diagonal onto -phase alpha e_1
     std::vector<double> ar((size_t)k * k), ai((size_t)k * k);
@@ -213,7 +224,8 @@ void herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec) {
     }
     std::vector<double> Z((size_t)k * k, 0.0);
     for (int i = 0; i < k; ++i) Z[(size_t)i * k + i] = 1.0;
-    if (k > 1) tridiag_qr(k, d, e, Z);
+    bool converged = true;
+    if (k > 1) converged = tridiag_qr(k, d, e, Z);
     std::vector<int> order(k);
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });
@@ -241,6 +253,7 @@ void herm_eig_n(int k, const double* Ain, double* w, double* Vout, int nvec) {
             Vout[2 * ((size_t)c * k + i) + 1] = yi[i];
         }
     }
+    return converged;
 }
 
 namespace {
@@ -250,7 +263,7 @@ namespace {
 // false) when a pivot falls below kMinPivot, i.e. when GB is too close to singular
 // for the factor to be trusted; the caller then takes the SVQB route.
 bool rr_cholesky(int k, const double* GA, const double* GB, const std::vector<double>& dsc, int nwant,
-                 double* theta, double* C, int* nout) {
+                 double* theta, double* C, int* nout, bool* qr_ok) {
     constexpr double kMinPivot = 1e-4;
     const size_t kk = (size_t)k * k;
     // L row-major (real and imaginary parts), lower triangle, row by row
@@ -323,7 +336,7 @@ bool rr_cholesky(int k, const double* GA, const double* GB, const std::vector<do
     }
     const int nv = std::min(nwant, k);
     std::vector<double> th(k), V(2 * (size_t)k * nv);
-    herm_eig_n(k, M.data(), th.data(), V.data(), nv);
+    *qr_ok = herm_eig_n(k, M.data(), th.data(), V.data(), nv);
     // C = D L^{-H} V (back substitution with L^H)
     for (int j = 0; j < nv; ++j) {
         theta[j] = th[j];
@@ -357,7 +370,9 @@ int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double d
         dsc[i] = (b > 0.0) ? 1.0 / std::sqrt(b) : 0.0;
     }
     int nout = 0;
-    if (try_cholesky && rr_cholesky(k, GA, GB, dsc, nwant, theta, C, &nout)) return nout;
+    bool qr_ok = true;
+    if (try_cholesky && rr_cholesky(k, GA, GB, dsc, nwant, theta, C, &nout, &qr_ok))
+        return qr_ok ? nout : kRRNoConv;
     std::vector<double> Bs(2 * (size_t)k * k);
     for (int j = 0; j < k; ++j)
         for (int i = 0; i < k; ++i) {
@@ -366,7 +381,7 @@ int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double d
             Bs[o + 1] = GB[o + 1] * dsc[i] * dsc[j];
         }
     std::vector<double> mu(k), U(2 * (size_t)k * k);
-    herm_eig(k, Bs.data(), mu.data(), U.data());
+    if (!herm_eig(k, Bs.data(), mu.data(), U.data())) return kRRNoConv;
     const double mmax = std::max(mu[k - 1], 1e-300);
     std::vector<int> keep;
     for (int i = 0; i < k; ++i)
@@ -399,7 +414,7 @@ int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double d
         }
     std::vector<double> th(kk), V(2 * (size_t)kk * kk);
     nout = std::min(nwant, kk);
-    herm_eig_n(kk, M.data(), th.data(), V.data(), nout);
+    if (!herm_eig_n(kk, M.data(), th.data(), V.data(), nout)) return kRRNoConv;
     for (int j = 0; j < nout; ++j) {
         theta[j] = th[j];
         for (int i = 0; i < k; ++i) {

@@ -154,6 +154,10 @@ int host_rr(fame_ctx* c, const Small& sm, int k, int m, int implicit_xx, const s
     const int got = rayleigh_ritz(k, GA.data(), GB.data(), m, drop, theta.data(),
                                   reinterpret_cast<double*>(Cm.data()), try_cholesky);
     c->stats_rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (got == kRRNoConv) {
+        *err = set_err(c, FAME_E_NOCONV, "Rayleigh-Ritz: the implicit QR of the small eigenproblem did not converge");
+        return -1;
+    }
     *err = FAME_OK;
     return got;
 }
@@ -209,6 +213,10 @@ int host_rr_refine(fame_ctx* c, const Small& sm, int m, int nq, const std::vecto
     const int got = rayleigh_ritz(k, GA.data(), GB.data(), m, drop, theta.data(),
                                   reinterpret_cast<double*>(Cm.data()));
     c->stats_rr_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (got == kRRNoConv) {
+        *err = set_err(c, FAME_E_NOCONV, "Rayleigh-Ritz: the implicit QR of the small eigenproblem did not converge");
+        return -1;
+    }
     *err = FAME_OK;
     return got;
 }

@@ -18,7 +18,9 @@
 // and Lambda_l are evaluated in the kernels from exact fractions.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "fame_internal.h"
 #include "fft2.cuh"
@@ -705,9 +707,20 @@ __global__ void __launch_bounds__(512) k_xy2(KParams<R> P, typename cpx<R>::T* _
 // ---------------------------------------------------------------------------
 constexpr size_t kSmemCap = 200 * 1024;
 
+// The dynamic shared-memory limit is one value per kernel for the whole process, and
+// contexts on other host threads (the batched solver's workers) launch the same
+// kernels with other sizes: the limit is only ever raised, under a lock, and the
+// largest value set so far is kept per kernel.
 template <typename R>
 fame_status set_smem(fame_ctx* c, const void* fn, size_t bytes) {
-    if (bytes > 48 * 1024) FAME_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> limit;
+    if (bytes <= 48 * 1024) return FAME_OK;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = limit.find(fn);
+    if (it != limit.end() && it->second >= bytes) return FAME_OK;
+    FAME_CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    limit[fn] = bytes;
     return FAME_OK;
 }
 

@@ -149,6 +149,15 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _check_out(out, like):
+    """A caller-provided output is written through its data pointer in the dense layout:
+    it must be contiguous and on the device of the input."""
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    if not out.is_cuda or out.device != like.device:
+        raise ValueError("out must be a CUDA tensor on the device of the input")
+
+
 def _dtype_code(t):
     import torch
     if t.dtype == torch.complex64:
@@ -243,6 +252,10 @@ class Context:
             raise ValueError("y must hold m vectors of 2n entries")
         if out is None:
             out = torch.empty_like(y)
+        elif out.shape != y.shape or out.dtype != y.dtype:
+            raise ValueError("out must have the shape and dtype of y")
+        else:
+            _check_out(out, y)
         _check(load().fame_apply_Ar(self._h, _ptr(y), _ptr(out), m, _dtype_code(y), _stream(stream)),
                self._h)
         return out
@@ -254,6 +267,7 @@ class Context:
         m = y.numel() // (2 * self.N)
         if m * 2 * self.N != y.numel() or out.shape != y.shape or out.dtype != y.dtype:
             raise ValueError("y must hold m vectors of 2n entries and out must match it")
+        _check_out(out, y)
         _check(load().fame_apply_Ar_static(self._h, _ptr(y), _ptr(out), m, _dtype_code(y),
                                            _stream(stream)), self._h)
         return out

@@ -5,8 +5,9 @@
 // residuals and the GB-orthonormality of its vectors are checked against the
 // mathematics rather than against another implementation.
 //
-// Usage: host_rr_check <spectrum> <k> <m> <cholesky 0|1> <seed>
-// Prints: "theta_err <e> resid <r> orth <o> got <n>" (errors relative to max |lambda|).
+// Usage: host_rr_check <spectrum> <k> <m> <cholesky 0|1> <seed> [total qr sweep limit]
+// Prints: "theta_err <e> resid <r> orth <o> got <n>" (errors relative to max |lambda|;
+// got = -2 when the implicit QR ran out of sweeps).
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -18,11 +19,13 @@
 
 int rayleigh_ritz(int k, const double* GA, const double* GB, int nwant, double drop, double* theta, double* C,
                   bool try_cholesky);
+void rr_set_qr_sweep_limit(int total);
 
 using cd = std::complex<double>;
 
 int main(int argc, char** argv) {
-    if (argc != 6) return 2;
+    if (argc != 6 && argc != 7) return 2;
+    if (argc == 7) rr_set_qr_sweep_limit(std::atoi(argv[6]));
     const char* spec = argv[1];
     const int k = std::atoi(argv[2]), m = std::atoi(argv[3]);
     const bool chol = std::atoi(argv[4]) != 0;

@@ -23,18 +23,31 @@ def _prof():
     }
 
 
-def test_bound_of_each_kind():
-    assert bench._bound("zin_c64")[:1] == ("hbm",)
-    assert bench._bound("xy_c64")[2] == "GB/s"
-    assert bench._bound("gram_c64")[:3] == ("alu", bench.FP32_PEAK_TFLOPS, "TFLOP/s")
-    assert bench._bound("combine_df_c128")[:2] == ("alu", bench.FP32_PEAK_TFLOPS)
-    assert bench._bound("xy_c128")[:2] == ("alu", bench.FP64_PEAK_TFLOPS)
+def test_bound_of_each_kind(monkeypatch):
+    monkeypatch.setattr(bench, "measured_peaks", lambda: (6746.0, "measured"))
+    P = _prof()
+    ridge32 = bench.FP32_PEAK_TFLOPS * 1e12 / 6746e9          # about 11.9 flop per byte
+    assert bench._bound("zin_c64", P["zin_c64"])[:1] == ("hbm",)
+    assert bench._bound("xy_c64", P["xy_c64"])[2] == "GB/s"
+    # 50 flop per byte: above the FP32 ridge
+    assert bench._bound("gram_c64", P["gram_c64"])[:3] == ("alu", bench.FP32_PEAK_TFLOPS, "TFLOP/s")
+    # the same kind below the ridge is HBM bound
+    low = {"flops": 0.5 * ridge32 * 1e9, "bytes": 1e9}
+    assert bench._bound("gram_c64", low)[:2] == ("hbm", 6746.0)
+    # double-float update: 8 flops per complex multiply-add over its bytes, against the FP32 ridge
+    df = {"flops": 5.7 * 1e9, "bytes": 1e9}
+    assert bench._bound("combine_df_c128", df)[:1] == ("hbm",)
+    assert bench._bound("combine_df_c128", {"flops": 2 * ridge32 * 1e9, "bytes": 1e9})[:2] == \
+        ("alu", bench.FP32_PEAK_TFLOPS)
+    # complex128 FFT pass: above the (low) FP64 ridge
+    assert bench._bound("xy_c128", P["xy_c128"])[:2] == ("alu", bench.FP64_PEAK_TFLOPS)
     # 152 SMs x 128 lanes x 2 flops x 2.07 GHz
     assert bench.FP32_PEAK_TFLOPS == pytest.approx(80.54784)
 
 
 def test_roofline_takes_dominant_kernel(monkeypatch):
     monkeypatch.setattr(bench, "traffic_for", lambda name: None)
+    monkeypatch.setattr(bench, "measured_peaks", lambda: (6746.0, "measured"))
     r = bench.roofline(_prof())
     assert r["kernel"] == "gram_c64" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(40e9 / 2.0e-3 / 1e12)          # flops per second
@@ -105,6 +118,6 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
-    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["cpu_baseline"]["cores"] == os.cpu_count() and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}

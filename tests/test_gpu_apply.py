@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 
 from oracle.lattice import make_lattice, with_kappa
 from oracle.nfsep import apply_Ar, lift, bases, basis_margin, G_TOL
+from oracle.spectral import lambdas
 from paper_1806_10284_gb300 import fame
 from paper_1806_10284_gb300 import workloads as W
 
@@ -97,15 +98,40 @@ def test_apply_gamma_point(prec):
     assert abs(got[0]) == 0.0 and abs(got[lat.n]) == 0.0
 
 
-def test_apply_basis_switch_points():
-    """Simple cubic at Gamma: Lambda parallel to (1,1,1) on the diagonal p = q = r; the
-    alternate reference vector is taken on both sides."""
-    lat, ctx, invB, rng = _setup("sc16", (8, 8, 8), kred=np.zeros(3))
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n", [(8, 8, 8),        # generic passes
+                               (16, 16, 16),     # fixed-length Z 16 and XY 16x16 (complex64)
+                               (64, 64, 16)])    # fixed-length XY 64x64, 512-thread form
+def test_apply_basis_switch_points(n, prec):
+    """Simple cubic at Gamma: Lambda parallel to (1,1,1) on the diagonal p = q = r, where
+    the paper's range basis is undefined; both sides take the alternate reference vector
+    there (the decision is taken in FP64 and shared by the complex64 kernels)."""
+    lat, ctx, invB, rng = _setup("sc16", n, kred=np.zeros(3))
+    L = np.stack(lambdas(lat))
+    Lq = np.sum(np.abs(L) ** 2, axis=0)
+    g = 3.0 * Lq - np.abs(L.sum(axis=0)) ** 2
+    assert np.count_nonzero((Lq > 0) & (g < G_TOL * 3.0 * Lq)) > 0       # alternate reference vector in use
+    if n[0] == n[1] == n[2]:
+        assert np.count_nonzero((Lq > 0) & (g <= 1e-12 * Lq)) >= n[0] - 1  # exact degeneracies present
     y = rng.standard_normal((2, 2 * lat.n)) + 1j * rng.standard_normal((2, 2 * lat.n))
-    got = ctx.apply(torch.as_tensor(y, device="cuda")).cpu().numpy()
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    got = ctx.apply(torch.as_tensor(y, dtype=dt, device="cuda")).cpu().numpy()
     for j in range(2):
         ref = apply_Ar(lat, y[j].reshape((2,) + lat.shape), invB).ravel()
-        assert _rel(got[j], ref) < TOL64
+        assert _rel(got[j], ref) < (TOL64 if prec == "c128" else TOL32)
+
+
+@pytest.mark.parametrize("name,n", [("fcc64", (16, 16, 16)), ("bcc96", (24, 24, 24)),
+                                    ("tri192", (32, 32, 48))])
+def test_apply_complex64_without_basis_margin(name, n):
+    """Complex64 applies at Bloch vectors chosen with no distance from the basis switch
+    (frequencies may sit on either side of it, arbitrarily close)."""
+    lat, ctx, invB, rng = _setup(name, n, seed=17, margin=0.0)
+    y = rng.standard_normal((2, 2 * lat.n)) + 1j * rng.standard_normal((2, 2 * lat.n))
+    got = ctx.apply(torch.as_tensor(y, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    for j in range(2):
+        ref = apply_Ar(lat, y[j].reshape((2,) + lat.shape), invB).ravel()
+        assert _rel(got[j], ref) < TOL32
 
 
 @pytest.mark.parametrize("m", [1, 7, 40])

@@ -36,9 +36,9 @@ def driver(tmp_path_factory):
     return exe
 
 
-def _run(exe, spectrum, k, m, chol, seed=1):
-    r = subprocess.run([exe, spectrum, str(k), str(m), str(int(chol)), str(seed)], capture_output=True, text=True,
-                       timeout=120)
+def _run(exe, spectrum, k, m, chol, seed=1, sweeps=None):
+    args = [exe, spectrum, str(k), str(m), str(int(chol)), str(seed)] + ([str(sweeps)] if sweeps else [])
+    r = subprocess.run(args, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     f = r.stdout.split()
     return dict(theta=float(f[1]), resid=float(f[3]), orth=float(f[5]), got=int(f[7]))
@@ -61,3 +61,14 @@ def test_rayleigh_ritz_sizes(driver, k, m):
         out = _run(driver, "spread", k, m, chol)
         assert out["got"] == m
         assert out["theta"] < 1e-12 and out["resid"] < 1e-12 and out["orth"] < 1e-11, (k, m, chol, out)
+
+
+@pytest.mark.parametrize("chol", [True, False])
+def test_rayleigh_ritz_reports_qr_that_runs_out_of_sweeps(driver, chol):
+    """An implicit QR stopped after a few sweeps, far too few to deflate 45 eigenvalues,
+    must be reported (got = -2) rather than returned as converged pairs; the same
+    pencil converges under the default limit."""
+    out = _run(driver, "spread", 45, 15, chol)
+    assert out["got"] == 15 and out["theta"] < 1e-12
+    out = _run(driver, "spread", 45, 15, chol, sweeps=3)
+    assert out["got"] == -2, out
