@@ -57,7 +57,8 @@ typedef enum {
     FAME_E_NOMEM = 5,    /* device or host allocation failed                           */
     FAME_E_STATE = 6,    /* call out of order (e.g. gradient before eigs, no eps set)   */
     FAME_E_NOCONV = 7,   /* eigensolver hit max_iter before the residual tolerance      */
-    FAME_E_TIMEOUT = 8   /* a bounded device wait gave up (batched solver)              */
+    FAME_E_TIMEOUT = 8   /* a bounded device wait of a tensor-core kernel gave up       */
+                         /* (limit: environment FAME_WAIT_TIMEOUT_MS, default 1000)      */
 } fame_status;
 
 /* dtype of vectors passed to fame_apply_Ar / fame_lift */
@@ -260,6 +261,25 @@ FAME_API fame_status fame_get_stats(const fame_ctx* ctx, fame_solve_stats* stats
  */
 FAME_API fame_status fame_grad_eps(fame_ctx* ctx, int nev, const double* dobj_dlambda, double rel_cluster,
                           double* dB_out, void* stream);
+
+/*
+ * fame_block_gram -- G = U^H V, the block inner products from which the eigensolver
+ * forms its Rayleigh-Ritz projections of eq. NFSEP (no counterpart in the paper,
+ * whose inverse Lanczos needs only vector inner products; exposed for callers that
+ * build their own projections, and for testing).
+ *   U : device [ku][2n] complex of type dtype (ku vectors of A_r length, vector-major).
+ *   V : device [kv][2n] complex of type dtype.
+ *   G : device [kv][ku] complex128, column-major: G[j ku + i] = sum_r conj(U_i[r]) V_j[r].
+ *   ku, kv in [1, 4096]; dtype FAME_C64 or FAME_C128.
+ * Complex64 blocks with at most 128 vectors on each side are multiplied on the tensor
+ * cores (tcgen05, TF32 operands split into high and low parts: about 2^-21 relative
+ * accuracy per product, FP32 sums within a row block, FP64 across row blocks); other
+ * shapes use FP32 (complex64) or FP64 (complex128) products.  Asynchronous on stream.
+ * Errors: FAME_E_ARG, FAME_E_NOMEM, FAME_E_CUDA.  If a bounded device wait of the
+ * tensor-core kernel gives up, G is filled with NaN.
+ */
+FAME_API fame_status fame_block_gram(fame_ctx* ctx, const void* U, int ku, const void* V, int kv, int dtype,
+                                     void* G, void* stream);
 
 /*
  * fame_eigs_batched -- solve several contexts (lattices and Bloch vectors along

@@ -313,6 +313,24 @@ fame_status fame_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double 
                             static_cast<cudaStream_t>(stream));
 }
 
+fame_status fame_block_gram(fame_ctx* c, const void* U, int ku, const void* V, int kv, int dtype, void* G,
+                            void* stream) {
+    if (check_ctx(c)) return FAME_E_ARG;
+    if (!U || !V || !G || ku < 1 || kv < 1 || ku > 4096 || kv > 4096)
+        return set_err(c, FAME_E_ARG, "bad U/V/G/ku/kv");
+    const size_t ld = 2 * (size_t)c->n;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fame_status s = tc_reset_err(c, st);
+    if (s != FAME_OK) return s;
+    if (dtype == FAME_C64)
+        return block_gram<float2>(c, static_cast<const float2*>(U), ku, static_cast<const float2*>(V), kv, ld,
+                                  static_cast<double2*>(G), st);
+    if (dtype == FAME_C128)
+        return block_gram<double2>(c, static_cast<const double2*>(U), ku, static_cast<const double2*>(V), kv, ld,
+                                   static_cast<double2*>(G), st);
+    return set_err(c, FAME_E_ARG, "dtype must be FAME_C64 or FAME_C128");
+}
+
 void fame_destroy(fame_ctx* c) {
     if (!c) return;
     free_tables(c);
@@ -321,6 +339,7 @@ void fame_destroy(fame_ctx* c) {
     if (c->solver2.p) cudaFree(c->solver2.p);
     if (c->partial.p) cudaFree(c->partial.p);
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
+    if (c->tcerr.p) cudaFree(c->tcerr.p);
     if (c->Y) cudaFree(c->Y);
     delete c;
 }

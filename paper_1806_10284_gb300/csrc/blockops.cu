@@ -3,6 +3,7 @@
 // preconditioner, and precision conversion.  Vectors are 2n complex, stored
 // vector-major ([m][2n]).
 #include <algorithm>
+#include <cstdlib>
 #include <cstdint>
 #include <mutex>
 #include <unordered_map>
@@ -13,6 +14,17 @@
 
 namespace {
 
+// Complex64 Grams whose wider side has at least this many vectors run on the tensor
+// cores (tc_gram.cu); narrower ones on the FP32 ring kernel, which is faster there
+// (measured at 64^3 and 96^3: 15 x 30 vectors 116 against 187 us; 30 x 75: 356 against
+// 250 us; 45 x 90: 556 against 408 us).
+// The environment variable FAME_TC_MIN_WIDTH overrides the threshold (e.g. 1: every shape
+// the tensor-core kernel takes).
+int tc_min_width() {
+    const char* v = std::getenv("FAME_TC_MIN_WIDTH");
+    return v ? std::max(1, std::atoi(v)) : 64;
+}
+
 // Gram kernel: GT x GT complex outputs per thread, GROWS rows per shared-memory stage
 constexpr int GT = 4;
 constexpr int GROWS = 32;
@@ -20,6 +32,21 @@ constexpr int GROWS = 32;
 // stage, stages in flight, outputs per thread group
 constexpr int kStRows = 128, kStCols = 8, kStStages = 4, kStOut = 16;
 static_assert(kStOut % kStCols == 0, "a group's outputs span whole stages");
+
+// Refinement form of the ring-staged combine (k_combine_st<.., RF = true>): the inputs
+// are [X32 | Q] with X32 the complex64 copy of the complex128 block X64 (its first mx
+// columns); for each output j the entries M[i][j] of j's block (blk[j] = count, then
+// the columns i) are taken from X64 in double-float arithmetic, all other entries
+// from the complex64 inputs in FP32.  Outputs Xn64 (complex128) and X32n (its
+// complex64 copy, may be null).
+constexpr int kRefBlk = kRefineBlock;
+struct RefineEpi {
+    const double2* X64 = nullptr;
+    int mx = 0;
+    const int* blk = nullptr;       // device [m][kRefBlk + 1]
+    double2* Xn64 = nullptr;
+    float2* X32n = nullptr;
+};
 
 template <typename C> struct Acc;
 template <> struct Acc<float2> { using T = float; };
@@ -505,10 +532,11 @@ __global__ void __launch_bounds__(kCombineThreads) k_combine(BlockList<C> S, siz
 // chunks (and of the next tile) are in flight while a chunk is consumed.  Columns
 // are visited in the order i0..k-1, 0..i0-1 with one accumulator: out2 is stored
 // when the first group of columns is complete, out1 at the end.
-template <typename Co, int G>
+template <typename Co, int G, bool RF = false>
 __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(BlockList<float2> S, size_t ld,
                                                              const double2* __restrict__ M, int m, int i0,
-                                                             Co* __restrict__ out1, Co* __restrict__ out2) {
+                                                             Co* __restrict__ out1, Co* __restrict__ out2,
+                                                             RefineEpi rf = RefineEpi{}) {
     using Ro = decltype(Co().x);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int nthr = G * kStRows, mo = G * kStOut;
@@ -520,10 +548,37 @@ __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(Bl
     float4* cf = reinterpret_cast<float4*>(smem_raw);
     float2* stage = reinterpret_cast<float2*>(cf + (size_t)kp * (mo / 2));   // [stages][cols][rows]
     const float2** ps = reinterpret_cast<const float2**>(stage + kStStages * kStCols * kStRows);
+    // refinement form: the double-float coefficients of each output's block, [mo][kRefBlk]
+    // as (re h, re l, im h, im l), and the block table [mo][kRefBlk + 1]
+    float4* cfd = reinterpret_cast<float4*>(ps + ((k + 1) & ~1));
+    int* blk = reinterpret_cast<int*>(cfd + (RF ? mo * kRefBlk : 0));
+    if constexpr (RF) {
+        for (int e = tid; e < mo * (kRefBlk + 1); e += nthr) {
+            const int j = e / (kRefBlk + 1);
+            blk[e] = j < m ? rf.blk[e] : 0;
+        }
+        __syncthreads();
+        for (int e = tid; e < mo * kRefBlk; e += nthr) {
+            const int j = e / kRefBlk, t = e - j * kRefBlk;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < blk[j * (kRefBlk + 1)]) {
+                const double2 v = M[(size_t)j * k + blk[j * (kRefBlk + 1) + 1 + t]];
+                const df64::Split a = df64::split(v.x), b = df64::split(v.y);
+                w = make_float4(a.h, a.l, b.h, b.l);
+            }
+            cfd[e] = w;
+        }
+    }
     for (int e = tid; e < kp * mo; e += nthr) {
         const int pos = e / mo, j = e - pos * mo;
         const int i = pos < k - first ? first + pos : pos - (k - first);
-        const double2 v = (j < m && pos < k) ? M[(size_t)j * k + i] : make_double2(0.0, 0.0);
+        double2 v = (j < m && pos < k) ? M[(size_t)j * k + i] : make_double2(0.0, 0.0);
+        if constexpr (RF) {
+            // entries of an output's own block are summed in double-float below
+            if (j < m && i < rf.mx)
+                for (int t = 0; t < blk[j * (kRefBlk + 1)]; ++t)
+                    if (blk[j * (kRefBlk + 1) + 1 + t] == i) v = make_double2(0.0, 0.0);
+        }
         reinterpret_cast<float2*>(cf)[e] = make_float2((float)v.x, (float)v.y);
     }
     for (int pos = tid; pos < k; pos += nthr) {
@@ -599,6 +654,30 @@ __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(Bl
                 if (j0 + j >= m) break;
                 if (out1) out1[(size_t)(j0 + j) * ld + row] = mk((Ro)acc[j].x, (Ro)acc[j].y);
                 if (out2 && first == k) out2[(size_t)(j0 + j) * ld + row] = mk((Ro)0, (Ro)0);   // empty second sum
+            }
+            if constexpr (RF) {
+                // Xn_j = sum over the block of j of X_i M[i][j] (complex128 inputs, double-float
+                // sums) + the FP32 sum of everything else
+#pragma unroll
+                for (int j = 0; j < kStOut; ++j) {
+                    const int jj = j0 + j;
+                    if (jj >= m) break;
+                    const int* b = blk + jj * (kRefBlk + 1);
+                    float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f;
+                    for (int t = 0; t < b[0]; ++t) {
+                        const double2 x = rf.X64[(size_t)b[1 + t] * ld + row];
+                        const df64::Split xr = df64::split(x.x), xi = df64::split(x.y);
+                        const float4 w = cfd[jj * kRefBlk + t];
+                        df64::mac(Sr, Er, xr.h, xr.l, w.x, w.y);
+                        df64::mac(Sr, Er, -xi.h, -xi.l, w.z, w.w);
+                        df64::mac(Si, Ei, xr.h, xr.l, w.z, w.w);
+                        df64::mac(Si, Ei, xi.h, xi.l, w.x, w.y);
+                    }
+                    const float er = Er + acc[j].x, ei = Ei + acc[j].y;
+                    const size_t o = (size_t)jj * ld + row;
+                    rf.Xn64[o] = make_double2(df64::widen(Sr) + df64::widen(er), df64::widen(Si) + df64::widen(ei));
+                    if (rf.X32n) rf.X32n[o] = make_float2(Sr + er, Si + ei);
+                }
             }
         }
     }
@@ -714,10 +793,11 @@ size_t orth_st_smem(int m, int groups) {
            (size_t)kStStages * kStCols * kStRows * sizeof(float2) + (size_t)groups * kStOut * sizeof(void*);
 }
 
-size_t combine_st_smem(int k, int groups) {
+size_t combine_st_smem(int k, int groups, bool refine = false) {
     const int kp = (k + kStCols - 1) / kStCols * kStCols;
     return (size_t)kp * groups * kStOut * sizeof(float2) +
-           (size_t)kStStages * kStCols * kStRows * sizeof(float2) + (size_t)k * sizeof(void*);
+           (size_t)kStStages * kStCols * kStRows * sizeof(float2) + (size_t)((k + 1) & ~1) * sizeof(void*) +
+           (refine ? (size_t)groups * kStOut * (kRefBlk * sizeof(float4) + (kRefBlk + 1) * sizeof(int)) : 0);
 }
 
 // R_j = AX_j - theta_j X_j;  W_j = tinv .* R_j (tinv indexed by frequency, both coordinates);
@@ -988,6 +1068,11 @@ fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, si
                  double2* G, cudaStream_t st) {
     const int ku = U.total, kv = V.total;
     if constexpr (std::is_same<CU, float2>::value && std::is_same<CV, float2>::value) {
+        if (tensor_cores_enabled() && std::max(ku, kv) >= tc_min_width()) {
+            // the wider side on the 128-row MMA operand
+            const fame_status s = kv >= ku ? gram_tc(c, V, U, ld, 1, G, st) : gram_tc(c, U, V, ld, 0, G, st);
+            if (s != FAME_E_ARG) return s;
+        }
         const int tiles = ((ku + GT - 1) / GT) * ((kv + GT - 1) / GT);
         const int ts = (tiles + 31) / 32 * 32;
         const size_t smem = gram_st_smem(ku, kv);
@@ -1052,10 +1137,27 @@ fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, si
 }
 
 template <typename C>
+fame_status block_gram(fame_ctx* c, const C* U, int ku, const C* V, int kv, size_t ld, double2* G,
+                       cudaStream_t st) {
+    fame_status s = gram<C, C>(c, blocks<C>(U, ku), blocks<C>(V, kv), ld, G, st);
+    if (s != FAME_OK) return s;
+    FAME_CUDA_TRY(c, cudaGetLastError());
+    return FAME_OK;
+}
+template fame_status block_gram<float2>(fame_ctx*, const float2*, int, const float2*, int, size_t, double2*, cudaStream_t);
+template fame_status block_gram<double2>(fame_ctx*, const double2*, int, const double2*, int, size_t, double2*, cudaStream_t);
+
+template <typename C>
 fame_status gram_herm(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V, size_t ld, double2* G,
                       cudaStream_t st) {
     const int ku = U.total;
     if (V.total != ku) return set_err(c, FAME_E_ARG, "gram_herm: U and V differ in width");
+    if constexpr (std::is_same<C, float2>::value) {
+        if (tensor_cores_enabled() && 2 * ku >= tc_min_width()) {
+            const fame_status s = gram_tc(c, concat(U, V), U, ld, 2, G, st);
+            if (s != FAME_E_ARG) return s;
+        }
+    }
     const int T = (ku + GT - 1) / GT, tiles = T * (T + 1);
     const int groups = (tiles + kGramThreads - 1) / kGramThreads;
     int threads = (((tiles + groups - 1) / groups + 31) / 32) * 32;
@@ -1122,6 +1224,44 @@ fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2
         const size_t span = (size_t)(kCombineThreads / kCombineSlots) * CR;
         const unsigned nblk = (unsigned)std::min<size_t>(152 * 4, (ld + span - 1) / span);
         k_combine<C, Co><<<nblk, kCombineThreads, smem, st>>>(S, ld, M, m, i0, out1, out2);
+    }
+    count_launch();
+    FAME_CUDA_TRY(c, cudaGetLastError());
+    return FAME_OK;
+}
+
+fame_status combine_refine(fame_ctx* c, const double2* X64, const float2* X32, int m, const BlockList<float2>& Q,
+                           size_t ld, const double2* M, const int* blk, double2* Xn, float2* X32n, float2* Pn,
+                           cudaStream_t st) {
+    const BlockList<float2> S = concat(blocks<float2>(X32, m), Q);
+    if (!combine_st_ok(S, ld, m) || m < 1)
+        return set_err(c, FAME_E_ARG, "combine_refine: block layout not supported");
+    const int groups = (m + kStOut - 1) / kStOut, threads = groups * kStRows;
+    const size_t smem = combine_st_smem(S.total, groups, true);
+    const void* fn = groups == 1 ? (const void*)k_combine_st<float2, 1, true> : (const void*)k_combine_st<float2, 2, true>;
+    fame_status s = kernel_smem(c, fn, smem);
+    if (s != FAME_OK) return s;
+    int per_sm = 0;
+    FAME_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+    const size_t ntiles = (ld + kStRows - 1) / kStRows;
+    const unsigned nblk = (unsigned)std::max<size_t>(1, std::min<size_t>((size_t)152 * std::max(per_sm, 1), ntiles));
+    RefineEpi rf;
+    rf.X64 = X64;
+    rf.mx = m;
+    rf.blk = blk;
+    rf.Xn64 = Xn;
+    rf.X32n = X32n;
+    {
+        // algorithmic bytes: X64 and [X32 Q] read, Xn64, X32n, Pn written; 8 flops per complex MAC
+        const int nq = Q.total;
+        ProfScope ps(K_COMBINE_DF, true, st,
+                     (double)ld * (m * sizeof(double2) + (m + nq) * sizeof(float2) + m * sizeof(double2) +
+                                   (X32n ? m * sizeof(float2) : 0) + (Pn ? m * sizeof(float2) : 0)),
+                     8.0 * (double)ld * m * (m + nq));
+        if (groups == 1)
+            k_combine_st<float2, 1, true><<<nblk, threads, smem, st>>>(S, ld, M, m, m, nullptr, Pn, rf);
+        else
+            k_combine_st<float2, 2, true><<<nblk, threads, smem, st>>>(S, ld, M, m, m, nullptr, Pn, rf);
     }
     count_launch();
     FAME_CUDA_TRY(c, cudaGetLastError());

@@ -47,6 +47,14 @@ template <> struct RealOf<double2> { using T = double; };
 template <typename CU, typename CV>
 fame_status gram(fame_ctx* c, const BlockList<CU>& U, const BlockList<CV>& V, size_t ld, double2* G,
                  cudaStream_t st);
+// Tensor-core Gram (tc_gram.cu): P = A^H B for complex64 blocks with at most 128 columns
+// on each side, written to G as P (mode 0, MA x NB), P^H (mode 1, NB x MA) or, for
+// A = [U | V] and B = U with k = NB, [P[:k] | P[k:]^H] (mode 2, k x 2k).  FAME_E_ARG
+// (nothing launched) when the shapes, the alignment or the driver do not allow it.
+fame_status gram_tc(fame_ctx* c, const BlockList<float2>& A, const BlockList<float2>& B, size_t ld, int mode,
+                    double2* G, cudaStream_t st);
+// false when the environment sets FAME_NO_TC=1 (the FP32 CUDA-core kernels are used)
+bool tensor_cores_enabled();
 // G (column-major k x 2k) = [U^H U | U^H V] for V = A U with A Hermitian: only the
 // entries on or below the diagonal of each k x k block are computed (the others are 0)
 template <typename C>
@@ -69,6 +77,16 @@ fame_status residual_mixed(fame_ctx* c, const double2* X, const double2* AX, con
 // X32n = complex64 copy of Xn (may be null), Pn = Q M[m:] (may be null); Q may be empty
 fame_status combine_mixed(fame_ctx* c, const double2* X, int m, const BlockList<float2>& Q, size_t ld,
                           const double2* M, double2* Xn, float2* X32n, float2* Pn, cudaStream_t st);
+// The same update with the FP64-accurate part confined to blocks of outputs: for output j
+// the entries M[i][j] with i in j's block (blk: device int [m][kRefineBlock + 1] = count,
+// then the columns i) multiply the complex128 X64 in double-float arithmetic; every other
+// entry multiplies X32 (the complex64 copy of X64) or Q in FP32.  Exact to the FP32
+// rounding of the off-block terms, so the blocks must hold every entry of M[:m] that is
+// not small.  Xn (complex128), X32n (complex64 copy, may be null), Pn = Q M[m:] (may be null).
+constexpr int kRefineBlock = 6;
+fame_status combine_refine(fame_ctx* c, const double2* X64, const float2* X32, int m, const BlockList<float2>& Q,
+                           size_t ld, const double2* M, const int* blk, double2* Xn, float2* X32n, float2* Pn,
+                           cudaStream_t st);
 // Q <- Q - X cfs (cfs m x nq), in place; FP64 arithmetic when X is complex128
 template <typename CX, typename CQ>
 fame_status orth_against(fame_ctx* c, const CX* X, int m, const BlockList<CQ>& Q, size_t ld,

@@ -147,6 +147,7 @@ struct fame_ctx {
     GrowBuf solver2;               // complex128 blocks of the fallback phase (on demand)
     GrowBuf partial;               // Gram partial sums
     GrowBuf pinned;                // page-locked host mirror of the solver's small buffers
+    GrowBuf tcerr;                 // device flag: a bounded wait of a tensor-core kernel gave up (sticky)
     fame_solve_stats stats{};
     double stats_rr_ms = 0.0;
     std::string err;
@@ -163,6 +164,9 @@ fame_status set_err(fame_ctx* c, fame_status s, const std::string& msg);
     } while (0)
 
 fame_status grow(fame_ctx* c, GrowBuf& b, size_t bytes);
+// raise a kernel's dynamic shared-memory limit to smem (never lowered; thread safe) and
+// prefer the largest shared-memory carveout
+fame_status kernel_smem(fame_ctx* c, const void* fn, size_t smem);
 fame_status grow_pinned(fame_ctx* c, GrowBuf& b, size_t bytes);   // page-locked host memory
 void count_launch(int k = 1);
 
@@ -224,6 +228,16 @@ fame_status run_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, int
 bool xy3_wide_supported(int n1, int n2);
 fame_status run_basis_mask(fame_ctx* c);
 fame_status run_twist_tables(fame_ctx* c);
+
+// error flag of the tensor-core kernels (tc_gram.cu): cleared by tc_reset_err, set by
+// any CTA whose bounded wait gave up; tc_wait_failed reads it (synchronous)
+fame_status tc_reset_err(fame_ctx* c, cudaStream_t st);
+bool tc_wait_failed(fame_ctx* c);
+
+// G = U^H V for device blocks of 2n complex rows (blockops.cu)
+template <typename C>
+fame_status block_gram(fame_ctx* c, const C* U, int ku, const C* V, int kv, size_t ld, double2* G,
+                       cudaStream_t st);
 
 // solver (solver.cu)
 fame_status run_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol, int max_iter,

@@ -85,16 +85,19 @@ struct Small {
     double2* Cd;     // [k][m]
     double* theta;   // [m]
     double* part;    // [m][kResidBlocks]
+    int* blk;        // [m][kRefineBlock + 1] blocks of the refinement update
     double2* hG = nullptr;
     double2* hC = nullptr;
     double* htheta = nullptr;
     double* hpart = nullptr;
+    int* hblk = nullptr;
 };
 
 size_t small_bytes(int m) {
     const int k = 3 * m;
     return ((size_t)k * 2 * k * sizeof(double2) + 255) + ((size_t)k * m * sizeof(double2) + 255) +
-           (m * sizeof(double) + 255) + ((size_t)m * kResidBlocks * sizeof(double) + 255);
+           (m * sizeof(double) + 255) + ((size_t)m * kResidBlocks * sizeof(double) + 255) +
+           ((size_t)m * (kRefineBlock + 1) * sizeof(int) + 255);
 }
 
 Small carve_small(Carver& cv, int m) {
@@ -104,7 +107,53 @@ Small carve_small(Carver& cv, int m) {
     s.Cd = cv.take<double2>((size_t)k * m);
     s.theta = cv.take<double>(m);
     s.part = cv.take<double>((size_t)m * kResidBlocks);
+    s.blk = cv.take<int>((size_t)m * (kRefineBlock + 1));
     return s;
+}
+
+// Blocks of the refinement update X_new = X C_X + Q C_Q (C_X the leading m rows of the
+// k x m Ritz coefficients Cm): outputs i and j share a block when |C_X[i][j]| or
+// |C_X[j][i]| exceeds kCouple.  Inside a block the complex128 X is combined in
+// FP64-accurate arithmetic; the remaining entries of C_X are below kCouple, so their
+// FP32 products carry errors below kCouple * 2^-24 relative.  Writes the table
+// [m][kRefineBlock + 1] (count, then the columns); false if a block is too large.
+constexpr double kCouple = 1e-4;
+bool refine_blocks(const std::vector<double2>& Cm, int k, int m, int* tab) {
+    std::vector<int> parent(m);
+    for (int i = 0; i < m; ++i) parent[i] = i;
+    auto find = [&](int i) {
+        while (parent[i] != i) i = parent[i] = parent[parent[i]];
+        return i;
+    };
+    for (int j = 0; j < m; ++j)
+        for (int i = 0; i < m; ++i) {
+            const double2 v = Cm[(size_t)j * k + i];
+            if (i != j && std::hypot(v.x, v.y) > kCouple) parent[find(i)] = find(j);
+        }
+    std::vector<std::vector<int>> members(m);
+    for (int i = 0; i < m; ++i) members[find(i)].push_back(i);
+    for (int j = 0; j < m; ++j) {
+        const std::vector<int>& b = members[find(j)];
+        if ((int)b.size() > kRefineBlock) return false;
+        int* row = tab + (size_t)j * (kRefineBlock + 1);
+        row[0] = (int)b.size();
+        for (int t = 0; t < kRefineBlock; ++t) row[1 + t] = t < (int)b.size() ? b[t] : 0;
+    }
+    return true;
+}
+
+bool gram_finite(const double2* G, size_t cnt) {
+    for (size_t i = 0; i < cnt; ++i)
+        if (!std::isfinite(G[i].x) || !std::isfinite(G[i].y)) return false;
+    return true;
+}
+
+// a non-finite Gram matrix: a tensor-core wait that gave up (reported as such), or
+// non-finite vectors
+fame_status gram_failure(fame_ctx* c) {
+    if (tc_wait_failed(c))
+        return set_err(c, FAME_E_TIMEOUT, "a bounded wait of the tensor-core Gram kernel gave up");
+    return set_err(c, FAME_E_NOCONV, "non-finite Gram matrix");
 }
 
 struct PhaseOut {
@@ -125,6 +174,10 @@ int host_rr(fame_ctx* c, const Small& sm, int k, int m, int implicit_xx, const s
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         *err = set_err(c, FAME_E_CUDA, std::string("Gram readback: ") + cudaGetErrorString(e));
+        return -1;
+    }
+    if (!gram_finite(G, (size_t)2 * k * k)) {
+        *err = gram_failure(c);
         return -1;
     }
     const auto t0 = std::chrono::steady_clock::now();
@@ -175,6 +228,10 @@ int host_rr_refine(fame_ctx* c, const Small& sm, int m, int nq, const std::vecto
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         *err = set_err(c, FAME_E_CUDA, std::string("Gram readback: ") + cudaGetErrorString(e));
+        return -1;
+    }
+    if (!gram_finite(G, cnt)) {
+        *err = gram_failure(c);
         return -1;
     }
     const auto t0 = std::chrono::steady_clock::now();
@@ -458,8 +515,17 @@ fame_status lob_refine(fame_ctx* c, float2* const S[2], float2* const AS[2], dou
         theta = th;
         if ((s = upload_rr(c, sm, Cm, theta, st)) != FAME_OK) return s;
         const int nxt = cur ^ 1;
-        if ((s = combine_mixed(c, X64[cur], m, Q, ld, sm.Cd, X64[nxt], S[nxt], S[nxt] + (size_t)2 * m * ld, st)) != FAME_OK) return s;
-        if ((s = combine_mixed(c, AX64[cur], m, AQ, ld, sm.Cd, AX64[nxt], AS[nxt], AS[nxt] + (size_t)2 * m * ld, st)) != FAME_OK) return s;
+        if (refine_blocks(Cm, m + nq, m, sm.hblk)) {
+            // FP64-accurate sums only inside the blocks of strongly coupled outputs; the
+            // complex64 copies X32 = S[cur], AX32 = AS[cur] carry the small remainder
+            FAME_CUDA_TRY(c, cudaMemcpyAsync(sm.blk, sm.hblk, (size_t)m * (kRefineBlock + 1) * sizeof(int),
+                                             cudaMemcpyHostToDevice, st));
+            if ((s = combine_refine(c, X64[cur], S[cur], m, Q, ld, sm.Cd, sm.blk, X64[nxt], S[nxt], S[nxt] + (size_t)2 * m * ld, st)) != FAME_OK) return s;
+            if ((s = combine_refine(c, AX64[cur], AS[cur], m, AQ, ld, sm.Cd, sm.blk, AX64[nxt], AS[nxt], AS[nxt] + (size_t)2 * m * ld, st)) != FAME_OK) return s;
+        } else {
+            if ((s = combine_mixed(c, X64[cur], m, Q, ld, sm.Cd, X64[nxt], S[nxt], S[nxt] + (size_t)2 * m * ld, st)) != FAME_OK) return s;
+            if ((s = combine_mixed(c, AX64[cur], m, AQ, ld, sm.Cd, AX64[nxt], AS[nxt], AS[nxt] + (size_t)2 * m * ld, st)) != FAME_OK) return s;
+        }
         np = m;
         cur = nxt;
     }
@@ -480,6 +546,7 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
     c->stats = fame_solve_stats{};
     c->stats_rr_ms = 0.0;
     fame_status s;
+    if ((s = tc_reset_err(c, st)) != FAME_OK) return s;
     const int k = 3 * m;
     size_t bytes = small_bytes(m) + 256;
     if (mixed)
@@ -498,6 +565,7 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
         sm.hC = h.Cd;
         sm.htheta = h.theta;
         sm.hpart = h.part;
+        sm.hblk = h.blk;
     }
     const uint64_t seed = 0x5eedF00Dull ^ ((uint64_t)c->n << 20) ^ (uint64_t)nev;
     const bool warm = (flags & FAME_WARM_START) && c->Y && c->Y_nev >= 1;

@@ -41,6 +41,8 @@ _SIGS = {
                             C.POINTER(C.c_int), C.c_void_p]),
     "fame_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fame_grad_eps": (C.c_int, [C.c_void_p, C.c_int, _D3, C.c_double, C.c_void_p, C.c_void_p]),
+    "fame_block_gram": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                  C.c_void_p]),
     "fame_eigs_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
                                     C.c_int, _D3, C.POINTER(C.c_int), C.c_void_p]),
     "fame_profile": (C.c_int, [C.c_int]),
@@ -271,6 +273,20 @@ class Context:
         _check(load().fame_apply_Ar_static(self._h, _ptr(y), _ptr(out), m, _dtype_code(y),
                                            _stream(stream)), self._h)
         return out
+
+    def block_gram(self, U, V, stream=None):
+        """G = U^H V (complex128 CUDA tensor [kv][ku], column-major in the C sense: G[j][i] =
+        sum conj(U_i) V_j) for U (ku, 2n) and V (kv, 2n) of one complex dtype (fame_block_gram)."""
+        import torch
+        U = U.contiguous()
+        V = V.contiguous()
+        if U.dtype != V.dtype or U.shape[-1] != 2 * self.N or V.shape[-1] != 2 * self.N:
+            raise ValueError("U and V must be (k, 2n) tensors of one complex dtype")
+        ku, kv = U.numel() // (2 * self.N), V.numel() // (2 * self.N)
+        G = torch.empty((kv, ku), dtype=torch.complex128, device=U.device)
+        _check(load().fame_block_gram(self._h, _ptr(U), ku, _ptr(V), kv, _dtype_code(U), _ptr(G),
+                                      _stream(stream)), self._h)
+        return G
 
     # -- apply plans and the autotuner --------------------------------------
     def apply_plan(self, dtype=FAME_C64):

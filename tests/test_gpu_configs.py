@@ -12,8 +12,8 @@ through the C ABI, against the CPU oracle.
   size.
 * Differentiable band gap (simple cubic 48^3, smooth eps on grid nodes, edge-mean
   B_l): d obj / d eps for obj = sum over the 8 Bloch vectors of
-  (lambda_6 - lambda_5) / lambda_5, from the adjoint gradient, against central
-  differences (step 1e-4) at 64 seeded node voxels, for FP64 and mixed solves.
+  (lambda_6 - lambda_5) / lambda_5, from the adjoint gradient of FP64 and of mixed
+  solves, against central differences (step 1e-4) at 64 seeded node voxels.
 """
 import json
 import os
@@ -83,51 +83,88 @@ def _edges(e):
             0.5 * (e + np.roll(e, -1, axis=0))]
 
 
-@pytest.mark.parametrize("flags", [fame.FAME_FP64, fame.FAME_MIXED])
-def test_config_sc48_band_gap_gradient_64_voxels_8_bloch_vectors(flags):
+def test_config_sc48_band_gap_gradient_64_voxels_8_bloch_vectors():
     """obj = sum_k (lambda_6(k) - lambda_5(k)) / lambda_5(k) over the workload's 8 Bloch
     vectors; the adjoint d obj / d eps at 64 seeded node voxels (chain rule through the
-    edge means) against central differences of the objective (step 1e-4).  The
-    perturbed solves start from the previous solve's eigenvectors (FAME_WARM_START) and
-    converge to residual 1e-12, so the eigenvalue differences are resolved to far below
-    the tolerance."""
+    edge means), from FP64 solves and from mixed solves, against central differences of
+    the objective (step 1e-4).  The differences come from FP64 solves that start from the
+    previous solve's eigenvectors (FAME_WARM_START) and converge to residual 1e-11.
+
+    Error budget of a central difference: truncation O(h^2) (below 1e-6 relative here)
+    plus (|e+| + |e-|) / 2h from the rounding error e of each computed objective.  The
+    eigenvalues carry rounding of order 1e-14 lambda from the FP64 transforms and Gram
+    sums, whatever the residual, and with h = 1e-4 a voxel moves the objective by only
+    about 1e-9: that term dominates.  The test samples the rounding as the spread s of
+    the objective at the unperturbed eps over five re-solves from other starting blocks
+    (floored at 1e-15 per Bloch vector); the largest of the 128 objective errors of the
+    differences is taken as 3 s (about three standard deviations), so the budget is
+    2e-4 relative plus 2 x 3 s / 2h."""
     w = W.WORKLOADS["sc48grad"]
     eps0, _ = W.smooth_field_eps(w["n"], w["seed"])
     Ks = W.bloch_vectors("sc48grad")
     assert len(Ks) == 8
     ctxs = [fame.Context(w["vectors"], w["n"], K) for K in Ks]
+    tol = 1e-11
 
-    def solve(ctx, B, warm):
+    def solve(ctx, B, flags, warm):
         ctx.set_eps(*B)
-        return ctx.eigs(6, tol=1e-12, max_iter=800, flags=flags | (fame.FAME_WARM_START if warm else 0))[0]
+        return ctx.eigs(6, tol=tol, max_iter=800, flags=flags | (fame.FAME_WARM_START if warm else 0))[0]
+
+    def objective(B):
+        total = 0.0
+        for ctx in ctxs:
+            lam = solve(ctx, B, fame.FAME_FP64, True)
+            total += (lam[5] - lam[4]) / lam[4]
+        return total
 
     B0 = _edges(eps0)
-    g = np.zeros_like(eps0)
-    for ctx in ctxs:
-        lam = solve(ctx, B0, False)
-        assert (lam[5] - lam[4]) > 1e-6 * lam[4]           # band 5 and 6 not degenerate
-        d = np.zeros(6)
-        d[5], d[4] = 1.0 / lam[4], -lam[5] / lam[4] ** 2
-        gB = ctx.grad(6, d, rel_cluster=1e-8).cpu().numpy().reshape((3,) + eps0.shape)
-        g += 0.5 * (gB[0] + np.roll(gB[0], 1, axis=2)) + 0.5 * (gB[1] + np.roll(gB[1], 1, axis=1)) \
-            + 0.5 * (gB[2] + np.roll(gB[2], 1, axis=0))
+
+    def adjoint(flags):
+        g = np.zeros_like(eps0)
+        obj = 0.0
+        for ctx in ctxs:
+            lam = solve(ctx, B0, flags, False)
+            assert (lam[5] - lam[4]) > 1e-6 * lam[4]           # band 5 and 6 not degenerate
+            obj += (lam[5] - lam[4]) / lam[4]
+            d = np.zeros(6)
+            d[5], d[4] = 1.0 / lam[4], -lam[5] / lam[4] ** 2
+            gB = ctx.grad(6, d, rel_cluster=1e-8).cpu().numpy().reshape((3,) + eps0.shape)
+            g += 0.5 * (gB[0] + np.roll(gB[0], 1, axis=2)) + 0.5 * (gB[1] + np.roll(gB[1], 1, axis=1)) \
+                + 0.5 * (gB[2] + np.roll(gB[2], 1, axis=0))
+        return g, obj
+
+    g_mixed, _ = adjoint(fame.FAME_MIXED)
+    g_fp64, obj0 = adjoint(fame.FAME_FP64)
     rng = np.random.default_rng(w["kseed"] + 1)
     voxels = set()
     while len(voxels) < 64:
         voxels.add(tuple(int(rng.integers(0, s)) for s in eps0.shape))
+    voxels = sorted(voxels)
+    # rounding of the objective: re-solve the unperturbed problem starting from the
+    # eigenvectors of problems perturbed at other voxels
+    spread = 0.0
+    for v in voxels[:5]:
+        e = eps0.copy()
+        e[v] += 1e-3
+        objective(_edges(e))
+        spread = max(spread, abs(objective(B0) - obj0))
+    noise = max(spread, 1e-15 * len(ctxs))
     h = 1e-4
-    for v in sorted(voxels):
+    fd = []
+    for v in voxels:
         vals = []
         for sgn in (1, -1):
             e = eps0.copy()
             e[v] += sgn * h
-            B = _edges(e)
-            total = 0.0
-            for ctx in ctxs:
-                lam = solve(ctx, B, True)
-                total += (lam[5] - lam[4]) / lam[4]
-            vals.append(total)
-        fd = (vals[0] - vals[1]) / (2 * h)
-        assert g[v] == pytest.approx(fd, rel=2e-4, abs=1e-9), (v, g[v], fd)
+            vals.append(objective(_edges(e)))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    for name, g in (("fp64", g_fp64), ("mixed", g_mixed)):
+        gv = np.array([g[v] for v in voxels])
+        use = np.abs(gv - fd) / (2e-4 * np.abs(fd) + 3.0 * noise / h)
+        rel = np.sort(np.abs(gv - fd) / np.abs(fd))
+        print(f"band-gap FD ({name} adjoint): rounding of obj {noise:.2e}, |g - fd| / |fd| median "
+              f"{rel[len(rel) // 2]:.2e} max {rel[-1]:.2e}, worst budget use {use.max():.2f}")
+        assert use.max() <= 1.0, (name, voxels[int(np.argmax(use))], use.max())
     for ctx in ctxs:
         ctx.close()
