@@ -243,7 +243,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FFT_PASSES = ("zin", "xy", "zout", "ypass", "xpass")
 
 
-KERNEL_SOURCES = ("apply3.cu", "blockops.cu", "transforms.cu", "eps.cu", "noalloc.cu", "tc_gram.cu", "tc.cuh", "fft2.cuh",
+KERNEL_SOURCES = ("apply3.cu", "blockops.cu", "transforms.cu", "eps.cu", "noalloc.cu", "tc_gram.cu", "precond.cu", "tc.cuh", "fft2.cuh",
                   "phases.cuh", "df64.cuh", "fame_internal.h", "blockops.h")
 
 

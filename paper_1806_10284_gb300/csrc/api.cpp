@@ -340,6 +340,7 @@ void fame_destroy(fame_ctx* c) {
     if (c->partial.p) cudaFree(c->partial.p);
     if (c->pinned.p) cudaFreeHost(c->pinned.p);
     if (c->tcerr.p) cudaFree(c->tcerr.p);
+    if (c->cheb.p) cudaFree(c->cheb.p);
     if (c->Y) cudaFree(c->Y);
     delete c;
 }

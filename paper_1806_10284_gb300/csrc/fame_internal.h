@@ -137,6 +137,8 @@ struct fame_ctx {
     uint32_t* alt_mask = nullptr;  // reference-vector decision per frequency (FP64)
     bool eps_set = false;
     double mean_invB = 0.0;
+    double min_invB = 0.0, max_invB = 0.0;   // spectrum bounds of Q_r^* B^{-1} Q_r
+    GrowBuf cheb;                  // Chebyshev preconditioner blocks (complex64)
     GrowBuf work;                  // transform workspace [m][3][n] complex
     ApplyPlan apply_plan[2];       // per dtype (FAME_C64, FAME_C128), set by fame_set_apply_plan / fame_autotune
     // solver state
@@ -172,7 +174,7 @@ void count_launch(int k = 1);
 
 // kernel kinds for the opt-in profiler (profile.cpp)
 enum KernelKind { K_ZIN, K_XY, K_ZOUT, K_YPASS, K_XPASS, K_GRAM, K_GRAM_RED, K_COMBINE, K_RESID,
-                  K_CONVERT, K_GRAD, K_SETUP, K_GRAM_HERM, K_ORTH, K_COMBINE_DF, K_COUNT };
+                  K_CONVERT, K_GRAD, K_SETUP, K_GRAM_HERM, K_ORTH, K_COMBINE_DF, K_PRECOND, K_COUNT };
 // Brackets a launch with events on its stream when profiling is on; attaches the
 // launch's algorithmic bytes and flops.
 class ProfScope {
@@ -238,6 +240,12 @@ bool tc_wait_failed(fame_ctx* c);
 template <typename C>
 fame_status block_gram(fame_ctx* c, const C* U, int ku, const C* V, int kv, size_t ld, double2* G,
                        cudaStream_t st);
+
+// Preconditioner of the block eigensolver (precond.cu): W <- S P_K(M) S (W / (S^2/mean)),
+// W given as tinv .* R, its ncols columns replaced by the Chebyshev inexact A_r^{-1} R
+template <typename C>
+fame_status precond_cheb(fame_ctx* c, C* W, int ncols, cudaStream_t st);
+int cheb_degree();
 
 // solver (solver.cu)
 fame_status run_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double tol, int max_iter,

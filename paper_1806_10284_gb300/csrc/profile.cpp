@@ -40,7 +40,7 @@ Prof& prof() {
 
 const char* kNames[K_COUNT] = {"zin", "xy", "zout", "ypass", "xpass", "gram", "gram_reduce",
                                "combine", "resid", "convert", "grad_accum", "setup", "gram_herm",
-                               "orth", "combine_df"};
+                               "orth", "combine_df", "precond"};
 
 }  // namespace
 

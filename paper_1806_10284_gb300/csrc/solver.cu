@@ -382,6 +382,7 @@ fame_status lob_explicit(fame_ctx* c, C* const S[2], C* const AS[2], const Small
             // ortho-LOBPCG (Hetmaniuk and Lehoucq 2006): W and P orthogonalised against X
             // (AP alongside), then AW for the orthogonalised W
             C* Wn = X + (size_t)m * ld + (size_t)j0 * ld;
+            if ((s = precond_cheb<C>(c, Wn, nw, st)) != FAME_OK) return s;
             C* Pn = X + (size_t)2 * m * ld;
             C* APn = AX + (size_t)2 * m * ld;
             const BlockList<C> Q = blocks<C>(Wn, nw, Pn, np);
@@ -489,6 +490,7 @@ fame_status lob_refine(fame_ctx* c, float2* const S[2], float2* const AS[2], dou
         j0 = leading_converged(res, nev, 0.5 * tol);
         nw = m - j0;
         float2* Wb = X32 + (size_t)m * ld + (size_t)j0 * ld;
+        if ((s = precond_cheb<float2>(c, Wb, nw, st)) != FAME_OK) return s;
         float2* AWb = AX32 + (size_t)m * ld + (size_t)j0 * ld;
         float2* Pb = X32 + (size_t)2 * m * ld;
         float2* APb = AX32 + (size_t)2 * m * ld;
