@@ -69,7 +69,8 @@ enum {
     FAME_FP64 = 1,          /* complex128 applies throughout                          */
     FAME_MIXED = 2,         /* complex64 applies, then complex128 refinement          */
     FAME_DETERMINISTIC = 4, /* fixed reduction order (always true in this build)      */
-    FAME_WARM_START = 8     /* start from the context's last eigenvectors if present  */
+    FAME_WARM_START = 8,    /* start from the context's last eigenvectors if present  */
+    FAME_INV_LANCZOS = 16   /* the paper's solver: Lanczos on A_r^{-1}, inner CG       */
 };
 
 /* Geometry chosen by fame_create (Section 2.2), for sampling eps on the Yee points. */
@@ -236,8 +237,19 @@ FAME_API fame_status fame_lift(fame_ctx* ctx, const void* y, void* x, int m, int
  *   Y_out      : device [nev][2][n] complex128 unit eigenvectors, or NULL.
  *   iters_out  : host int (total iterations), or NULL.
  * The eigenpairs are also kept in the context for fame_grad_eps.
+ * FAME_INV_LANCZOS (instead of FAME_MIXED / FAME_FP64) runs the paper's solver
+ * (Section 5.2; settings of Section 6): Lanczos on A_r^{-1} with full
+ * reorthogonalisation, each A_r^{-1} q = S M^{-1} S q (S = Sigma_r^{-1},
+ * M = Q_r^* B^{-1} Q_r) by an unpreconditioned complex128 CG to relative residual
+ * min(tol, 1e-13); converged when the Ritz estimates of the nev largest eigenvalues
+ * theta of A_r^{-1} are <= tol theta (the paper uses tol = 1e-12); at most
+ * min(max_iter, 160) Lanczos steps.  The explicit residuals ||A_r y - lambda y|| /
+ * lambda are then measured (complex128 apply) and reported in max_residual;
+ * iters_out is the number of Lanczos steps, stats.iters_mixed the inner CG
+ * iterations in all.
  * Synchronises stream.  Errors: FAME_E_ARG, FAME_E_STATE, FAME_E_NOCONV
- * (lambda_out still holds the best values), FAME_E_NOMEM, FAME_E_CUDA.
+ * (lambda_out still holds the best values), FAME_E_NOMEM, FAME_E_CUDA,
+ * FAME_E_TIMEOUT (a tensor-core wait gave up).
  */
 FAME_API fame_status fame_eigs(fame_ctx* ctx, int nev, double tol, int max_iter, int flags,
                       double* lambda_out, void* Y_out, int* iters_out, void* stream);
@@ -291,7 +303,12 @@ FAME_API fame_status fame_block_gram(fame_ctx* ctx, const void* U, int ku, const
  * every context keeps its eigenvectors as after fame_eigs.  The work starts
  * after the work already queued on stream.
  *   ctxs       : host array of nprob distinct context pointers (eps set on each).
- *   nev, tol, max_iter, flags : as fame_eigs (FAME_MIXED or FAME_FP64).
+ *   nev, tol, max_iter, flags : as fame_eigs (FAME_MIXED or FAME_FP64).  With
+ *                FAME_WARM_START the batch is read as band paths (Section 6): runs of
+ *                consecutive contexts on the same grid are cut into segments of at most
+ *                ceil(nprob / 8) problems, and inside a segment each problem starts from
+ *                the eigenvectors of the one before it (the first from random vectors);
+ *                segments run concurrently.
  *   lambda_out : host [nprob][nev] doubles.
  *   iters_out  : host [nprob] ints, or NULL.
  * Returns when every problem is done.  Errors: as fame_eigs (the first failing

@@ -265,9 +265,15 @@ fame_status fame_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags,
     if (check_ctx(c)) return FAME_E_ARG;
     if (nev < 1 || nev > 64 || !(tol > 0.0) || max_iter < 1 || !lambda_out)
         return set_err(c, FAME_E_ARG, "bad nev/tol/max_iter/lambda_out");
-    if (!(flags & (FAME_MIXED | FAME_FP64))) return set_err(c, FAME_E_ARG, "flags need FAME_MIXED or FAME_FP64");
+    if (!(flags & (FAME_MIXED | FAME_FP64 | FAME_INV_LANCZOS)))
+        return set_err(c, FAME_E_ARG, "flags need FAME_MIXED, FAME_FP64 or FAME_INV_LANCZOS");
     if (!c->eps_set) return set_err(c, FAME_E_STATE, "fame_set_eps has not been called");
     if (2LL * c->n < 3LL * (nev + 4)) return set_err(c, FAME_E_ARG, "grid too small for nev");
+    if (flags & FAME_INV_LANCZOS) {
+        fame_status s = tc_reset_err(c, static_cast<cudaStream_t>(stream));
+        if (s != FAME_OK) return s;
+        return run_inv_lanczos(c, nev, tol, max_iter, lambda_out, Y_out, iters_out, static_cast<cudaStream_t>(stream));
+    }
     return run_eigs(c, nev, tol, max_iter, flags, lambda_out, Y_out, iters_out,
                     static_cast<cudaStream_t>(stream));
 }

@@ -252,6 +252,9 @@ fame_status run_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double t
                              int flags, double* lambda_out, int* iters_out, cudaStream_t st);
 fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, double* lambda_out,
                      void* Y_out, int* iters_out, cudaStream_t st);
+// the paper's solver: Lanczos on A_r^{-1} with inner CG on Q_r^* B^{-1} Q_r (lanczos.cu)
+fame_status run_inv_lanczos(fame_ctx* c, int nev, double tol, int max_iter, double* lambda_out, void* Y_out,
+                            int* iters_out, cudaStream_t st);
 
 // small dense FP64 Rayleigh-Ritz (rr.cpp): solve GA c = theta GB c for the k x k
 // Hermitian pair (column-major complex, interleaved), return the nwant smallest

@@ -664,6 +664,28 @@ void lend(fame_ctx* c, BatchWorkspace& w) {
     std::swap(c->partial, w.partial);
 }
 
+// The eigenvectors of problem src as the start block of problem dst (same grid).
+fame_status seed_from(fame_ctx* dst, const fame_ctx* src, int nev, cudaStream_t st) {
+    if (!src->Y || src->Y_nev < 1) return FAME_E_STATE;
+    const int k = std::min(nev, src->Y_nev);
+    const size_t ld = 2 * (size_t)dst->n;
+    if (dst->Y_nev < k) {
+        if (dst->Y) cudaFree(dst->Y);
+        dst->Y = nullptr;
+        dst->Y_nev = 0;
+        if (cudaMalloc((void**)&dst->Y, (size_t)nev * ld * sizeof(double2)) != cudaSuccess) {
+            cudaGetLastError();
+            return FAME_E_NOMEM;
+        }
+        dst->Y_nev = nev;
+    }
+    if (cudaMemcpyAsync(dst->Y, src->Y, (size_t)k * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return FAME_E_CUDA;
+    }
+    return FAME_OK;
+}
+
 void release(BatchWorkspace& w) {
     for (GrowBuf* b : {&w.work, &w.solver, &w.solver2, &w.partial})
         if (b->p) cudaFree(b->p);
@@ -682,6 +704,29 @@ fame_status run_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double t
         return set_err(nullptr, FAME_E_CUDA, "batch: event on the caller's stream");
     }
     const int workers = std::min(nprob, kBatchWorkers);
+    // Work items: single problems, or with FAME_WARM_START segments of band paths --
+    // consecutive contexts on the same grid form a path, cut into segments of at most
+    // ceil(nprob / (2 workers)) problems; inside a segment each problem starts from its
+    // predecessor's eigenvectors (neighbouring Bloch vectors of a path have nearby
+    // eigenvectors in the frequency coordinates), the first one from random vectors.
+    const bool warm = (flags & FAME_WARM_START) != 0;
+    std::vector<std::pair<int, int>> items;     // [first, last) problems
+    if (warm) {
+        const int seg = std::max(1, (nprob + 2 * workers - 1) / (2 * workers));
+        int i = 0;
+        while (i < nprob) {
+            int j = i + 1;
+            while (j < nprob && j - i < seg && ctxs[j]->plan.n[0] == ctxs[i]->plan.n[0] &&
+                   ctxs[j]->plan.n[1] == ctxs[i]->plan.n[1] && ctxs[j]->plan.n[2] == ctxs[i]->plan.n[2] &&
+                   ctxs[j]->device == ctxs[i]->device)
+                ++j;
+            items.emplace_back(i, j);
+            i = j;
+        }
+    } else {
+        for (int i = 0; i < nprob; ++i) items.emplace_back(i, i + 1);
+    }
+    const int nitems = (int)items.size();
     std::atomic<int> next(0);
     std::vector<fame_status> status(nprob, FAME_OK);
     std::vector<fame_status> wstatus(workers, FAME_OK);
@@ -698,14 +743,20 @@ fame_status run_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double t
             }
             BatchWorkspace bw;
             for (;;) {
-                const int i = next.fetch_add(1);
-                if (i >= nprob) break;
-                fame_ctx* c = ctxs[i];
-                lend(c, bw);
-                int it = 0;
-                status[i] = fame_eigs(c, nev, tol, max_iter, flags, lambda_out + (size_t)i * nev, nullptr, &it, ws);
-                lend(c, bw);                  // the context gets its own buffers back
-                if (iters_out) iters_out[i] = it;
+                const int t = next.fetch_add(1);
+                if (t >= nitems) break;
+                for (int i = items[t].first; i < items[t].second; ++i) {
+                    fame_ctx* c = ctxs[i];
+                    int f = flags & ~FAME_WARM_START;
+                    if (i > items[t].first && status[i - 1] == FAME_OK &&
+                        seed_from(c, ctxs[i - 1], nev, ws) == FAME_OK)
+                        f |= FAME_WARM_START;
+                    lend(c, bw);
+                    int it = 0;
+                    status[i] = fame_eigs(c, nev, tol, max_iter, f, lambda_out + (size_t)i * nev, nullptr, &it, ws);
+                    lend(c, bw);              // the context gets its own buffers back
+                    if (iters_out) iters_out[i] = it;
+                }
             }
             if (cudaStreamSynchronize(ws) != cudaSuccess) wstatus[w] = FAME_E_CUDA;
             release(bw);

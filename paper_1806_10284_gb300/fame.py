@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libfame.so")
 
 FAME_C64, FAME_C128 = 0, 1
-FAME_FP64, FAME_MIXED, FAME_DETERMINISTIC, FAME_WARM_START = 1, 2, 4, 8
+FAME_FP64, FAME_MIXED, FAME_DETERMINISTIC, FAME_WARM_START, FAME_INV_LANCZOS = 1, 2, 4, 8, 16
 STATUS = {0: "FAME_OK", 1: "FAME_E_ARG", 2: "FAME_E_LATTICE", 3: "FAME_E_RADIX", 4: "FAME_E_CUDA",
           5: "FAME_E_NOMEM", 6: "FAME_E_STATE", 7: "FAME_E_NOCONV", 8: "FAME_E_TIMEOUT"}
 
