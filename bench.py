@@ -77,13 +77,28 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload_inputs(rank):
-    """Vectors, grid, Bloch vector of this rank (rank 0: the workload's own k)."""
+def problem_list(world):
+    """The independent eigenproblems of a run on ``world`` GPUs (weak scaling: one per
+    rank): the workload's Bloch vector and, for each further rank, a neighbouring one
+    (reduced coordinates moved by a fixed step)."""
     from paper_1806_10284_gb300 import workloads as W
     w = W.WORKLOADS[WORKLOAD]
-    red = np.array(w["reduced_k"][0], dtype=np.float64)
-    if rank > 0:
-        red = red + np.array([0.013, -0.007, 0.011]) * rank
+    base = np.array(w["reduced_k"][0], dtype=np.float64)
+    return [base + np.array([0.013, -0.007, 0.011]) * i for i in range(world)]
+
+
+def my_problems(rank, world):
+    """[(problem index, reduced Bloch vector)] of this rank: the round-robin share of
+    ``problem_list(world)`` (paper_1806_10284_gb300.sharding.shard)."""
+    from paper_1806_10284_gb300.sharding import shard
+    return shard(list(enumerate(problem_list(world))), rank, world)
+
+
+def workload_inputs(rank, world=1):
+    """Vectors, grid and Bloch vector of this rank's problem (rank 0: the workload's own k)."""
+    from paper_1806_10284_gb300 import workloads as W
+    w = W.WORKLOADS[WORKLOAD]
+    _, red = my_problems(rank, max(world, rank + 1))[0]
     return w["vectors"], w["n"], W.bloch_from_reduced(w["vectors"], red)
 
 
@@ -488,7 +503,7 @@ def run_ours(args, rank, world, local):
     from paper_1806_10284_gb300 import fame
     from paper_1806_10284_gb300 import workloads as W
     fame.load()
-    vec, n, K = workload_inputs(rank)
+    vec, n, K = workload_inputs(rank, world)
     ctx = fame.Context(vec, n, K, lattice=2)
     B = W.eps_for(WORKLOAD, ctx.geometry())
     ctx.set_eps(*B)
@@ -558,15 +573,13 @@ def run_ours(args, rank, world, local):
         prof_ms += e0.elapsed_time(e1)
     fame.profile(False)
     prof = fame.profile_read()
-    # max over ranks of the timed region, sum of work
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms, eig_ms], dtype=torch.float64, device="cuda")
-        a = torch.tensor([float(applies), float(launches)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(a, op=dist.ReduceOp.SUM)
-        total_ms, eig_ms = float(t[0]), float(t[1])
-        applies, launches = int(a[0]), int(a[1])
+    # max over ranks of the timed region, sum of work; every rank's eigenvalues to all
+    from paper_1806_10284_gb300.sharding import gather_results, reduce_timing
+    dev = torch.device("cuda", local)
+    total_ms, applies = reduce_timing(total_ms, float(applies), device=dev)
+    eig_ms, launches = reduce_timing(eig_ms, float(launches), device=dev)
+    applies, launches = int(applies), int(launches)
+    gathered = gather_results({idx: [float(x) for x in lam] for idx, _ in my_problems(rank, world)})
     value = applies / (total_ms / 1e3)
 
     # end to end through the public API with host buffers (pinned), H2D and D2H inside
@@ -585,13 +598,8 @@ def run_ours(args, rank, world, local):
         dB_h.copy_(dB)                                  # D2H of the gradient
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        a = torch.tensor([float(e2e_applies)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(a, op=dist.ReduceOp.SUM)
-        e2e_s, e2e_applies = float(t[0]), int(a[0])
+    e2e_ms, e2e_applies = reduce_timing(e2e_s * 1e3, float(e2e_applies), device=dev)
+    e2e_s = e2e_ms / 1e3
     extras = None
     if world == 1 and not args.no_extras:
         extras = comparisons(ctx, lam)
@@ -612,7 +620,8 @@ def run_ours(args, rank, world, local):
                       "nev": NEV, "tol": TOL, "block": m, "grid": list(n),
                       "l2": "512 MiB buffer written between timed steps (L2 flush); "
                             "solver working set > L2",
-                      "parallelism": f"{world} independent k-points (one per GPU)"},
+                      "parallelism": f"{world} independent k-points (one per GPU)",
+                      "problems_gathered": len(gathered)},
            "time_to_10_bands_s": eig_ms / args.steps / 1e3,
            "solve_stats": {k: st[k] for k in ("iters_mixed", "iters_fp64", "applies_c64", "applies_c128",
                                                "rr_host_ms")},

@@ -219,6 +219,22 @@ FAME_API fame_status fame_autotune(fame_ctx* ctx, int m, int dtype, double* best
 FAME_API fame_status fame_lift(fame_ctx* ctx, const void* y, void* x, int m, int dtype, void* stream);
 
 /*
+ * fame_fields -- the electric and magnetic fields of eigenpairs (lambda_j, y_j) of A_r
+ * on the Yee grid: E_j = B^{-1} Q_r Sigma_r y_j (the GEP eigenvector, as fame_lift) and
+ * H_j = C E_j / (i omega_j) = -i omega_j P_r y_j, omega_j = sqrt(lambda_j) (mu_0 = 1),
+ * with P_r = (I_3 (x) T)[P_1 P_2] the left singular vectors of C = P_r Sigma_r Q_r^*
+ * (eq. SVD, Section 5.1): per frequency P_r = C^ Pi_r / Sigma_r, C^ the curl symbol
+ * of C_l T = T Lambda_l.  Then C^* H_j = -i omega_j B E_j (Section 3).
+ *   y      : device [m][2][n] complex128 eigenvectors of A_r.
+ *   lambda : host, m eigenvalues (needed for H).
+ *   E, H   : device [m][3][n] complex128 each, or NULL for a field not wanted.
+ *   dtype  : FAME_C128.  Synchronises stream.
+ * Errors: FAME_E_ARG, FAME_E_STATE (no eps set), FAME_E_NOMEM, FAME_E_CUDA.
+ */
+FAME_API fame_status fame_fields(fame_ctx* ctx, const void* y, const double* lambda, void* E, void* H, int m,
+                                 int dtype, void* stream);
+
+/*
  * fame_eigs -- the nev smallest (nonzero) eigenvalues of A_r, which are the
  * nev smallest nonzero eigenvalues of C^*C e = lambda B e (eq. GEP; Theorem
  * invariant_space).  Block LOBPCG with the preconditioner

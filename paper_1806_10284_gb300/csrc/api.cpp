@@ -319,6 +319,18 @@ fame_status fame_eigs_batched(fame_ctx* const* ctxs, int nprob, int nev, double 
                             static_cast<cudaStream_t>(stream));
 }
 
+fame_status fame_fields(fame_ctx* c, const void* y, const double* lambda, void* E, void* H, int m, int dtype,
+                        void* stream) {
+    if (check_ctx(c)) return FAME_E_ARG;
+    if (!y || (!E && !H) || m < 1 || m > 4096) return set_err(c, FAME_E_ARG, "bad y/E/H/m");
+    if (H && !lambda) return set_err(c, FAME_E_ARG, "H needs the eigenvalues");
+    if (dtype != FAME_C128) return set_err(c, FAME_E_ARG, "fields are computed in complex128 (FAME_C128)");
+    if (!c->eps_set) return set_err(c, FAME_E_STATE, "fame_set_eps has not been called");
+    if (H && y == H) return set_err(c, FAME_E_ARG, "y and H must not overlap");
+    return run_fields(c, static_cast<const double2*>(y), lambda, static_cast<double2*>(E), static_cast<double2*>(H), m,
+                      static_cast<cudaStream_t>(stream));
+}
+
 fame_status fame_block_gram(fame_ctx* c, const void* U, int ku, const void* V, int kv, int dtype, void* G,
                             void* stream) {
     if (check_ctx(c)) return FAME_E_ARG;

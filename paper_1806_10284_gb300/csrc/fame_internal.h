@@ -95,6 +95,9 @@ struct KParams {
     const typename cpx<R>::T* lam3;    // [n3][n2][n1] Lambda_3 at frequency (p, q, r)
     const typename cpx<R>::T* tw2;     // [n2][n1] e^{2 pi i b f2(p)}, b the y index
     const typename cpx<R>::T* tw1;     // [n1] e^{2 pi i a f1}, a the x index
+    // Z-in expands Lambda x (Pi_r y) / Lambda_q instead of Sigma_r Pi_r y: the left
+    // singular vectors P_r y (eq. SVD) of the H field; the generic kernels only
+    int curl;
 };
 
 // Device tables of one precision.
@@ -210,6 +213,9 @@ fame_status run_apply_into(fame_ctx* c, const typename cpx<R>::T* y, typename cp
 template <typename R>
 fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* x, int m,
                      cudaStream_t st);
+// E = B^{-1} Q_r Sigma_r y and H = -i sqrt(lambda) P_r y for m eigenpairs (complex128)
+fame_status run_fields(fame_ctx* c, const double2* y, const double* lambda, double2* E, double2* H, int m,
+                       cudaStream_t st);
 fame_status run_grad(fame_ctx* c, const double2* Y, const double* w, int nev, double* dB,
                      cudaStream_t st);
 fame_status run_precond_table(fame_ctx* c, cudaStream_t st);

@@ -203,6 +203,24 @@ __device__ __forceinline__ void contract(const PencilBasis<R>& b, typename cpx<R
     z2 = (root(Lq) * r2) * xW;
 }
 
+// (o_0, o_1, o_2) <- Lambda x (o_0, o_1, o_2) / Lambda_q: applied to Sigma_r Pi_r y this
+// gives the frequency-side curl C^ Pi_r y / Sigma_r, C^ the 3 x 3 curl symbol with
+// C_l T = T Lambda_l (Section 4), i.e. the left singular vectors P_r y of eq. (SVD).
+template <typename C>
+__device__ __forceinline__ void curl_of(C L0, C L1, C L2, C& o0, C& o1, C& o2) {
+    using R = decltype(C().x);
+    const R Lq = L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y + L2.x * L2.x + L2.y * L2.y;
+    if (!(Lq > (R)0)) {
+        o0 = o1 = o2 = mk((R)0, (R)0);
+        return;
+    }
+    const R inv = (R)1 / Lq;
+    const C c0 = cmul(L1, o2) - cmul(L2, o1), c1 = cmul(L2, o0) - cmul(L0, o2), c2 = cmul(L0, o1) - cmul(L1, o0);
+    o0 = inv * c0;
+    o1 = inv * c1;
+    o2 = inv * c2;
+}
+
 template <typename C>
 __device__ __forceinline__ void load_table(C* dst, const C* src, int L) {
     for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];

@@ -236,6 +236,7 @@ static void fill_common(const fame_ctx* c, KParams<R>& k, const DevTables<R>& t)
     k.tw2 = t.tw2;
     k.tw1 = t.tw1;
     k.scale = (R)(1.0 / (double)c->n);
+    k.curl = 0;
 }
 
 template <>

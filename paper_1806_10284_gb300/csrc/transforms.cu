@@ -21,6 +21,7 @@
 #include <mutex>
 #include <type_traits>
 #include <unordered_map>
+#include <vector>
 
 #include "fame_internal.h"
 #include "fft2.cuh"
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(512) k_zin(KParams<R> P, const typename cpx<R>
                 o0 = cmul(b.p1[0], s1) + cmul(b.p2[0], s2);
                 o1 = cmul(b.p1[1], s1) + cmul(b.p2[1], s2);
                 o2 = cmul(b.p1[2], s1) + cmul(b.p2[2], s2);
+                if (P.curl) curl_of(L0s[pp], L1s[pp], L2, o0, o1, o2);
             }
             buf[e] = o0;
             buf[tile + e] = o1;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(512) k_xy(KParams<R> P, typename cpx<R>::T* __
     } else {
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int a = e % n1;
-            g[e] = (ib[e] * lift_scale) * cmul(cur[e], P.tw1[a]);
+            g[e] = (mode == 2 ? lift_scale : ib[e] * lift_scale) * cmul(cur[e], P.tw1[a]);
         }
     }
 }
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(256) k_xpass(KParams<R> P, typename cpx<R>::T*
         const int l = (int)((row / ((long long)n3 * n2)) % 3);
         const R ib = P.invB[(size_t)l * nsp + (size_t)rb * n1 + a];
         if (mode == 0) cur[e] = (ib * P.scale) * cur[e];
-        else cur[e] = (ib * lift_scale) * cmul(cur[e], P.tw1[a]);
+        else cur[e] = (mode == 2 ? lift_scale : ib * lift_scale) * cmul(cur[e], P.tw1[a]);
     }
     __syncthreads();
     if (mode == 0) cur = fft_axis(cur, oth, rows, P.ax[0], tw, false);
@@ -567,6 +569,7 @@ __global__ void __launch_bounds__(512) k_zin2(KParams<R> P, const typename cpx<R
                 const PencilBasis<R> pb{L0, L1, L0 + L1, L0 - L1,
                                         L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y};
                 expand<R>(pb, P.lam3[f], alt_bit(P.alt, f), y1, y2, o0, o1, o2);
+                if (P.curl) curl_of(L0, L1, P.lam3[f], o0, o1, o2);
             }
             X[r * NP + pp] = o0;
             X[r * NP + TP + pp] = o1;
@@ -697,7 +700,7 @@ __global__ void __launch_bounds__(512) k_xy2(KParams<R> P, typename cpx<R>::T* _
     } else {
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int b = fdiv(e, inv_n1), a = e - b * n1;
-            g[e] = (ib[e] * lift_scale) * cmul(X[b * S + a], P.tw1[a]);
+            g[e] = (mode == 2 ? lift_scale : ib[e] * lift_scale) * cmul(X[b * S + a], P.tw1[a]);
         }
     }
 }
@@ -970,6 +973,49 @@ fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::
     fame_status s;
     if ((s = z_pass<R>(c, P, y, x, m, true, st)) != FAME_OK) return s;
     return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
+}
+
+namespace {
+// H_j <- -i sqrt(lambda_j) H_j for the m fields [m][3n]
+__global__ void k_h_scale(double2* __restrict__ H, const double* __restrict__ w, int m, size_t N3) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)m * N3;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double s = w[i / N3];
+        const double2 h = H[i];
+        H[i] = make_double2(s * h.y, -s * h.x);
+    }
+}
+}  // namespace
+
+// E = B^{-1} Q_r Sigma_r y (the lift) and H = C E / (i omega) = -i omega P_r y,
+// omega = sqrt(lambda) (mu_0 = 1): since C = P_r Sigma_r Q_r^* on the range (eq. SVD)
+// and Sigma_r Q_r^* E = A_r y = lambda y for an eigenpair.  P_r y is the inverse
+// twisted DFT of the per-frequency curl symbol applied to Pi_r y (divided by Sigma_r).
+fame_status run_fields(fame_ctx* c, const double2* y, const double* lambda, double2* E, double2* H, int m,
+                       cudaStream_t st) {
+    if (m <= 0) return FAME_OK;
+    fame_status s;
+    if (E && (s = run_lift<double>(c, y, E, m, st)) != FAME_OK) return s;
+    if (!H) return FAME_OK;
+    KParams<double> P = make_params<double>(c);
+    P.curl = 1;
+    // the generic (two-level / Stockham) Z-in kernels implement the curl expansion
+    const ApplyPlan saved = c->apply_plan[FAME_C128];
+    if (!(saved.zfam == 2 || saved.zfam == 3)) c->apply_plan[FAME_C128].zfam = apply_zfam_available(c, FAME_C128, 2, m) ? 2 : 3;
+    s = z_pass<double>(c, P, y, H, m, true, st);
+    c->apply_plan[FAME_C128] = saved;
+    if (s != FAME_OK) return s;
+    if ((s = xy_stage<double>(c, P, H, m, 2, 1.0 / std::sqrt((double)c->n), st)) != FAME_OK) return s;
+    std::vector<double> w(m);
+    for (int j = 0; j < m; ++j) w[j] = std::sqrt(std::max(lambda[j], 0.0));
+    if ((s = grow(c, c->partial, (size_t)m * sizeof(double))) != FAME_OK) return s;
+    double* wd = static_cast<double*>(c->partial.p);
+    FAME_CUDA_TRY(c, cudaMemcpyAsync(wd, w.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_h_scale<<<1216, 256, 0, st>>>(H, wd, m, 3 * (size_t)c->n);
+    count_launch();
+    FAME_CUDA_TRY(c, cudaGetLastError());
+    FAME_CUDA_TRY(c, cudaStreamSynchronize(st));
+    return FAME_OK;
 }
 
 fame_status run_grad(fame_ctx* c, const double2* Y, const double* w, int nev, double* dB,

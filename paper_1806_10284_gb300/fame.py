@@ -41,6 +41,8 @@ _SIGS = {
                             C.POINTER(C.c_int), C.c_void_p]),
     "fame_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fame_grad_eps": (C.c_int, [C.c_void_p, C.c_int, _D3, C.c_double, C.c_void_p, C.c_void_p]),
+    "fame_fields": (C.c_int, [C.c_void_p, C.c_void_p, _D3, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                              C.c_void_p]),
     "fame_block_gram": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                   C.c_void_p]),
     "fame_eigs_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
@@ -273,6 +275,23 @@ class Context:
         _check(load().fame_apply_Ar_static(self._h, _ptr(y), _ptr(out), m, _dtype_code(y),
                                            _stream(stream)), self._h)
         return out
+
+    def fields(self, y, lam, want_e=True, want_h=True, stream=None):
+        """(E, H): complex128 CUDA tensors (m, 3n) of eigenpairs (lam[j], y[j]) (fame_fields);
+        E = B^{-1} Q_r Sigma_r y, H = -i sqrt(lam) P_r y.  Either may be skipped (None)."""
+        import torch
+        y = y.contiguous()
+        if y.dtype != torch.complex128:
+            raise TypeError("fields are computed from complex128 eigenvectors")
+        m = y.numel() // (2 * self.N)
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).ravel())
+        if lam.size != m:
+            raise ValueError("one eigenvalue per vector")
+        E = torch.empty((m, 3 * self.N), dtype=torch.complex128, device=y.device) if want_e else None
+        H = torch.empty((m, 3 * self.N), dtype=torch.complex128, device=y.device) if want_h else None
+        _check(load().fame_fields(self._h, _ptr(y), lam.ctypes.data_as(_D3), _ptr(E) if E is not None else None,
+                                  _ptr(H) if H is not None else None, m, FAME_C128, _stream(stream)), self._h)
+        return E, H
 
     def block_gram(self, U, V, stream=None):
         """G = U^H V (complex128 CUDA tensor [kv][ku], column-major in the C sense: G[j][i] =

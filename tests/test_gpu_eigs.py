@@ -352,3 +352,27 @@ def test_inverse_lanczos_fcc64_against_oracle_golden():
     np.testing.assert_allclose(lam, gold["eigenvalues"], rtol=1e-10)
     assert np.all(_residuals(ctx, lam, Y) <= 1e-8)
     ctx.close()
+
+
+@pytest.mark.parametrize("name,n", [("tri192", (8, 6, 5)), ("fcc64", (6, 6, 6))])
+def test_fields_against_sparse_curl(name, n):
+    """fame_fields: E = B^{-1} Q_r Sigma_r y against the oracle's lift, and H (via the left
+    singular vectors P_r of eq. SVD) against the oracle's explicit sparse curl,
+    H = C E / (i omega); then the other Maxwell equation C^* H = -i omega B E."""
+    from oracle.curl import curl
+    from oracle.nfsep import lift
+    lat, ctx, B = _small(name, n, seed=13)
+    nev = 6
+    lam, Y, _ = ctx.eigs(nev, tol=1e-12, flags=fame.FAME_FP64, vectors=True)
+    E, H = ctx.fields(Y, lam)
+    E, H, Yh = E.cpu().numpy(), H.cpu().numpy(), Y.cpu().numpy()
+    C = curl(lat)
+    Bd = B.ravel()
+    for j in range(nev):
+        e_ref = lift(lat, Yh[j].reshape((2,) + lat.shape), 1.0 / B).ravel()
+        assert np.abs(E[j] - e_ref).max() <= 1e-11 * np.abs(e_ref).max()
+        w = np.sqrt(lam[j])
+        h_ref = (C @ e_ref) / (1j * w)
+        assert np.abs(H[j] - h_ref).max() <= 1e-9 * np.abs(h_ref).max(), j
+        back = C.conj().T @ H[j]
+        assert np.abs(back + 1j * w * Bd * E[j]).max() <= 1e-9 * np.abs(w * Bd * E[j]).max()
