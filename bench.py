@@ -327,6 +327,15 @@ def roofline(prof):
             "share_of_kernel_time": st["total_ms"] / sum(v["total_ms"] for v in prof.values())}
 
 
+def kernel_table(prof):
+    """Per kernel kind of one profiled step: launches, device time, share, GB/s."""
+    tot = sum(v["total_ms"] for v in prof.values()) or 1e-9
+    return {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                "share": round(v["total_ms"] / tot, 4),
+                "GBps": v["bytes"] / max(v["total_ms"], 1e-9) / 1e6}
+            for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])}
+
+
 def apply_roofline(prof):
     """The fused complex64 FFT apply (Z-in, XY, Z-out together): pass-model bytes over time."""
     hbm, kind = measured_peaks()
@@ -634,9 +643,7 @@ def run_ours(args, rank, world, local):
            "roofline": rl,
            "apply_roofline": apply_roofline(prof),
            "apply_plan_c64": plan,
-           "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
-                           "GBps": v["bytes"] / max(v["total_ms"], 1e-9) / 1e6}
-                       for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])},
+           "kernels": kernel_table(prof),
            "e2e": {"value": e2e_applies / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": int(3 * ctx.N * 8),
                    "d2h_bytes_per_step": int(NEV * 8 + 3 * ctx.N * 8)},
@@ -769,7 +776,8 @@ def run_tri192(args, rank, world, local):
                       "l2": "working set (several GB) > L2"},
            "time_to_20_bands_s": total_ms / args.steps / 1e3, "per_step": per_k,
            "gpu_launches": launches, "clocks": clk, "roofline": rl, "apply_roofline": apply_roofline(prof),
-           "apply_plan_c64": plan, "fp64_per_bloch_vector": fp64, "oracle_check": checks,
+           "apply_plan_c64": plan, "kernels": kernel_table(prof), "fp64_per_bloch_vector": fp64,
+           "oracle_check": checks,
            "cpu_baseline": None, "e2e": None}
     print(json.dumps(out), flush=True)
     c.close()

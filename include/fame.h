@@ -237,9 +237,12 @@ FAME_API fame_status fame_fields(fame_ctx* ctx, const void* y, const double* lam
 /*
  * fame_eigs -- the nev smallest (nonzero) eigenvalues of A_r, which are the
  * nev smallest nonzero eigenvalues of C^*C e = lambda B e (eq. GEP; Theorem
- * invariant_space).  Block LOBPCG with the preconditioner
- * Sigma_r^{-2} / mean(B^{-1}); Gram matrices accumulated in FP64 and the
- * Rayleigh-Ritz problem solved in FP64.  With FAME_MIXED the iteration runs
+ * invariant_space).  Block LOBPCG with the preconditioner S P_K(M) S
+ * (S = Sigma_r^{-1}, M = Q_r^* B^{-1} Q_r, P_K the degree-K Chebyshev
+ * approximation of M^{-1} on [min 1/B, max 1/B]; K from the environment
+ * variable FAME_CHEB_DEGREE, default 3, K = 1 the diagonal Sigma_r^{-2} /
+ * mean(B^{-1})); Gram matrices accumulated in FP64 and the Rayleigh-Ritz
+ * problem solved in FP64.  With FAME_MIXED the iteration runs
  * on complex64 applies and is then refined with complex128 applies; with
  * FAME_FP64 it runs on complex128 throughout.  Converged when
  * ||A_r y_j - lambda_j y_j|| <= tol * lambda_j (||y_j|| = 1, complex128

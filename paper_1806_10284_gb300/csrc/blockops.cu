@@ -14,6 +14,13 @@
 
 namespace {
 
+// FP64 arithmetic on the FP64 units instead of double-float on the FP32 units (the
+// environment variable FAME_FP64_NATIVE=1; for comparisons)
+bool fp64_native() {
+    const char* v = std::getenv("FAME_FP64_NATIVE");
+    return v && v[0] == '1';
+}
+
 // Complex64 Grams whose wider side has at least this many vectors run on the tensor
 // cores (tc_gram.cu); narrower ones on the FP32 ring kernel, which is faster there
 // (measured at 64^3 and 96^3: 15 x 30 vectors 116 against 187 us; 30 x 75: 356 against
@@ -417,6 +424,119 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_herm(BlockList<C> U, Bloc
         for (int b = 0; b < GT; ++b) {
             const int i = ti * GT + a, j = tj * GT + b;
             if (i < ku && j < ku) out[(size_t)j * ku + i] = make_double2((double)accr[a][b], (double)acci[a][b]);
+        }
+}
+
+// The Hermitian Gram pair of k_gram_herm for complex128 blocks in double-float
+// arithmetic on the FP32 units (df64.cuh: Dekker's exact products with FMA, Knuth's
+// two-sum; about 2^-47 relative per sum), where the FP64 units of this GPU run at a
+// small fraction of the FP32 rate.  Same staging as k_gram_herm; after each stage
+// lands, every staged double is split once into a float pair (h, l) in shared
+// memory, then each thread accumulates a 2 x 2 tile of entries.
+constexpr int GT2 = 2;
+
+__global__ void __launch_bounds__(kGramThreads) k_gram_herm_df(BlockList<double2> U, BlockList<double2> V,
+                                                               size_t ld, size_t rows_per_blk,
+                                                               double2* __restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ku = U.total, SP = herm_stride(ku);
+    const int T = (ku + GT2 - 1) / GT2, ntri = T * (T + 1) / 2;
+    double2* su = reinterpret_cast<double2*>(smem_raw);              // [2][GROWS][SP]
+    double2* sv = su + 2 * GROWS * SP;                               // [2][GROWS][SP]
+    float4* hu = reinterpret_cast<float4*>(sv + 2 * GROWS * SP);     // [GROWS][SP]: (re h, re l, im h, im l)
+    float4* hv = hu + GROWS * SP;                                    // [GROWS][SP]
+    const double2** pu = reinterpret_cast<const double2**>(hv + GROWS * SP);
+    const double2** pv = pu + ku;
+    for (int i = threadIdx.x; i < ku; i += blockDim.x) {
+        pu[i] = col_ptr(U, i, ld);
+        pv[i] = col_ptr(V, i, ld);
+    }
+    for (int e = threadIdx.x; e < 2 * GROWS; e += blockDim.x)
+        for (int i = ku; i < SP; ++i) su[e * SP + i] = sv[e * SP + i] = make_double2(0.0, 0.0);
+    const int tile = blockIdx.y * blockDim.x + threadIdx.x;
+    const bool active = tile < 2 * ntri;
+    const int sblk = active ? tile / ntri : 0, tr = active ? tile - sblk * ntri : 0;
+    int ti = (int)((sqrtf(8.0f * tr + 1.0f) - 1.0f) * 0.5f);
+    while (ti * (ti + 1) / 2 > tr) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= tr) ++ti;
+    const int tj = tr - ti * (ti + 1) / 2;
+    const size_t r0 = blockIdx.x * rows_per_blk;
+    const size_t r1 = min(ld, r0 + rows_per_blk);
+    __syncthreads();
+    const auto stage = [su, sv, pu, pv, ku, SP, r1](size_t rb, int buf) {
+        const int nr = (int)min((size_t)GROWS, r1 - rb);
+        double2* du = su + buf * GROWS * SP;
+        double2* dv = sv + buf * GROWS * SP;
+        for (int e = threadIdx.x; e < GROWS * ku; e += blockDim.x) {
+            const int i = e / GROWS, t = e - i * GROWS;
+            const size_t off = rb + (t < nr ? t : 0);
+            cp_async_c(&du[t * SP + i], pu[i] + off, t < nr);
+            cp_async_c(&dv[t * SP + i], pv[i] + off, t < nr);
+        }
+        cp_async_commit();
+    };
+    float Sr[GT2][GT2], Er[GT2][GT2], Si[GT2][GT2], Ei[GT2][GT2];
+#pragma unroll
+    for (int a = 0; a < GT2; ++a)
+#pragma unroll
+        for (int b = 0; b < GT2; ++b) Sr[a][b] = Er[a][b] = Si[a][b] = Ei[a][b] = 0.f;
+    const int nst = (int)((r1 - r0 + GROWS - 1) / GROWS);
+    if (nst > 0) stage(r0, 0);
+    for (int st = 0; st < nst; ++st) {
+        if (st + 1 < nst) {
+            stage(r0 + (size_t)(st + 1) * GROWS, (st + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        {
+            const double2* bu = su + (st & 1) * GROWS * SP;
+            const double2* bv = sv + (st & 1) * GROWS * SP;
+            for (int e = threadIdx.x; e < GROWS * SP; e += blockDim.x) {
+                const double2 x = bu[e], y = bv[e];
+                const df64::Split a = df64::split(x.x), b = df64::split(x.y);
+                const df64::Split c = df64::split(y.x), d = df64::split(y.y);
+                hu[e] = make_float4(a.h, a.l, b.h, b.l);
+                hv[e] = make_float4(c.h, c.l, d.h, d.l);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const float4* bu = hu + ti * GT2;
+            const float4* bw = (sblk == 0 ? hu : hv) + tj * GT2;
+#pragma unroll 1
+            for (int t = 0; t < GROWS; ++t) {
+                float4 u[GT2], w[GT2];
+#pragma unroll
+                for (int a = 0; a < GT2; ++a) {
+                    u[a] = bu[t * SP + a];
+                    w[a] = bw[t * SP + a];
+                }
+#pragma unroll
+                for (int a = 0; a < GT2; ++a)
+#pragma unroll
+                    for (int b = 0; b < GT2; ++b) {
+                        // conj(u) w: re = ur wr + ui wi, im = ur wi - ui wr
+                        df64::mac(Sr[a][b], Er[a][b], u[a].x, u[a].y, w[b].x, w[b].y);
+                        df64::mac(Sr[a][b], Er[a][b], u[a].z, u[a].w, w[b].z, w[b].w);
+                        df64::mac(Si[a][b], Ei[a][b], u[a].x, u[a].y, w[b].z, w[b].w);
+                        df64::mac(Si[a][b], Ei[a][b], -u[a].z, -u[a].w, w[b].x, w[b].y);
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    double2* out = partial + (size_t)blockIdx.x * ku * 2 * ku + (size_t)sblk * ku * ku;
+#pragma unroll
+    for (int a = 0; a < GT2; ++a)
+#pragma unroll
+        for (int b = 0; b < GT2; ++b) {
+            const int i = ti * GT2 + a, j = tj * GT2 + b;
+            if (i < ku && j < ku)
+                out[(size_t)j * ku + i] = make_double2(df64::widen(Sr[a][b]) + df64::widen(Er[a][b]),
+                                                       df64::widen(Si[a][b]) + df64::widen(Ei[a][b]));
         }
 }
 
@@ -1185,6 +1305,52 @@ fame_status gram_herm(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V,
     count_launch(2);
     FAME_CUDA_TRY(c, cudaGetLastError());
     return FAME_OK;
+}
+
+// The Hermitian pair of Grams of complex128 blocks in double-float arithmetic on
+// the FP32 units (k_gram_herm_df): about 2^-47 relative per product against the
+// 2^-53 of native FP64, so only for blocks whose Gram is well conditioned -- the
+// Ritz confirmation of near-eigenvectors X, where AX ~ X Theta -- and never for the
+// LOBPCG blocks [X W P], whose W^H A W entries carry ||A|| / lambda amplification.
+// Native FP64 (k_gram_herm<double2>) where the double-float stages do not fit in
+// shared memory or FAME_FP64_NATIVE is set.
+fame_status gram_herm_df(fame_ctx* c, const BlockList<double2>& U, const BlockList<double2>& V, size_t ld,
+                         double2* G, cudaStream_t st) {
+    using C = double2;
+    const int ku = U.total;
+    if (V.total != ku) return set_err(c, FAME_E_ARG, "gram_herm_df: U and V differ in width");
+    if (!fp64_native()) {
+        const int T = (ku + GT2 - 1) / GT2, tiles = T * (T + 1);
+        const int groups = (tiles + kGramThreads - 1) / kGramThreads;
+        int threads = (((tiles + groups - 1) / groups + 31) / 32) * 32;
+        if (threads < 64) threads = 64;
+        const int SP = herm_stride(ku);
+        const size_t smem = (size_t)4 * GROWS * SP * sizeof(double2) + (size_t)2 * GROWS * SP * sizeof(float4) +
+                            (size_t)2 * ku * sizeof(void*);
+        if (smem <= 200u * 1024u) {
+            int nblk = 152 * 4;
+            size_t rpb = (ld + nblk - 1) / nblk;
+            rpb = ((rpb + GROWS - 1) / GROWS) * GROWS;
+            nblk = (int)((ld + rpb - 1) / rpb);
+            const int kk = ku * 2 * ku;
+            fame_status s = grow(c, c->partial, (size_t)nblk * kk * sizeof(double2));
+            if (s != FAME_OK) return s;
+            if ((s = kernel_smem(c, (const void*)k_gram_herm_df, smem)) != FAME_OK) return s;
+            double2* part = reinterpret_cast<double2*>(c->partial.p);
+            {
+                ProfScope ps(K_GRAM_HERM, true, st, (double)ld * 2 * ku * sizeof(C), 8.0 * ku * (ku + 1) * (double)ld);
+                k_gram_herm_df<<<dim3(nblk, groups), threads, smem, st>>>(U, V, ld, rpb, part);
+            }
+            {
+                ProfScope ps(K_GRAM_RED, true, st, (double)nblk * kk * sizeof(double2), 2.0 * nblk * kk);
+                k_gram_reduce<<<(kk + 7) / 8, 256, 0, st>>>(part, nblk, kk, G, ku);
+            }
+            count_launch(2);
+            FAME_CUDA_TRY(c, cudaGetLastError());
+            return FAME_OK;
+        }
+    }
+    return gram_herm<double2>(c, U, V, ld, G, st);
 }
 
 template <typename C, typename Co>

@@ -60,6 +60,11 @@ bool tensor_cores_enabled();
 template <typename C>
 fame_status gram_herm(fame_ctx* c, const BlockList<C>& U, const BlockList<C>& V, size_t ld, double2* G,
                       cudaStream_t st);
+// The same for complex128 blocks in double-float arithmetic on the FP32 units (about
+// 2^-47 relative per product): for well-conditioned Grams only, i.e. near-eigenvectors
+// U with V = A U ~ U Theta
+fame_status gram_herm_df(fame_ctx* c, const BlockList<double2>& U, const BlockList<double2>& V, size_t ld,
+                         double2* G, cudaStream_t st);
 // out1 = S M[:, :m], out2 = S[:, i0:] M[i0:, :m]  (either output may be null)
 template <typename C, typename Co>
 fame_status combine(fame_ctx* c, const BlockList<C>& S, size_t ld, const double2* M, int m, int i0,

@@ -180,6 +180,17 @@ enum KernelKind { K_ZIN, K_XY, K_ZOUT, K_YPASS, K_XPASS, K_GRAM, K_GRAM_RED, K_C
                   K_CONVERT, K_GRAD, K_SETUP, K_GRAM_HERM, K_ORTH, K_COMBINE_DF, K_PRECOND, K_COUNT };
 // Brackets a launch with events on its stream when profiling is on; attaches the
 // launch's algorithmic bytes and flops.
+// NVTX range on the calling host thread (header-only NVTX 3: a no-op branch unless a
+// profiler such as Nsight Systems or Nsight Compute is attached).  The solver marks
+// its phases with these, and every ProfScope marks its kernel pass.
+class NvtxRange {
+  public:
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 class ProfScope {
   public:
     ProfScope(int kind, bool dbl, cudaStream_t st, double bytes, double flops = 0.0);

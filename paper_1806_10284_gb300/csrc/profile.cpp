@@ -1,4 +1,8 @@
-// Opt-in per-kernel timing with CUDA events on the launching stream.
+// Opt-in per-kernel timing with CUDA events on the launching stream, and NVTX
+// ranges named for each kernel pass ("zin_c64", ...) that are always on.
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -42,10 +46,28 @@ const char* kNames[K_COUNT] = {"zin", "xy", "zout", "ypass", "xpass", "gram", "g
                                "combine", "resid", "convert", "grad_accum", "setup", "gram_herm",
                                "orth", "combine_df", "precond"};
 
+// "zin_c64", "zin_c128", ... in the order of the profiler's ids
+struct RangeNames {
+    char s[2 * K_COUNT][32];
+    RangeNames() {
+        for (int i = 0; i < 2 * K_COUNT; ++i)
+            std::snprintf(s[i], sizeof(s[i]), "%s_%s", kNames[i / 2], (i & 1) ? "c128" : "c64");
+    }
+};
+
+const RangeNames& range_names() {
+    static const RangeNames r;
+    return r;
+}
+
 }  // namespace
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 ProfScope::ProfScope(int kind, bool dbl, cudaStream_t st, double bytes, double flops)
     : id_(-1), st_(st), bytes_(bytes), flops_(flops), ev_(nullptr) {
+    nvtxRangePushA(range_names().s[kind * 2 + (dbl ? 1 : 0)]);
     Prof& p = prof();
     if (!p.on) return;
     std::lock_guard<std::mutex> g(p.mu);
@@ -56,6 +78,7 @@ ProfScope::ProfScope(int kind, bool dbl, cudaStream_t st, double bytes, double f
 }
 
 ProfScope::~ProfScope() {
+    nvtxRangePop();
     if (id_ < 0) return;
     Prof& p = prof();
     std::lock_guard<std::mutex> g(p.mu);

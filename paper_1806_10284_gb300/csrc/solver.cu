@@ -4,8 +4,9 @@
 // this library uses the block form, whose only operator access is a block of
 // A_r applies, so every FFT pass runs on m vectors at once.
 //
-// One iteration: R = AX - X Theta and W = T R with T = Sigma_r^{-2} / mean(B^{-1})
-// (exact for constant B); AW = A_r W for the columns not yet converged (soft
+// One iteration: R = AX - X Theta and W = T R with T = S P_K(M) S, the Chebyshev
+// approximation of A_r^{-1} (precond.cu; degree 1 is Sigma_r^{-2} / mean(B^{-1}),
+// exact for constant B); AW = A_r W for the columns not yet converged (soft
 // locking of the leading converged ones); Gram matrices of [X W P] against
 // [X W P | AX AW AP] accumulated in FP64; the FP64 Rayleigh-Ritz problem on a
 // GB-orthonormal basis (host); X <- S C, P <- S_{WP} C_{WP} and the same
@@ -20,8 +21,9 @@
 //            copies; their X-X blocks are the identity and Theta of the
 //            previous Rayleigh-Ritz step.  A complex128 apply starts the phase
 //            and confirms convergence.
-//   end      explicit FP64 Rayleigh-Ritz on X with a complex128 apply; the
-//            reported residuals ||A_r y - lambda y|| / lambda come from it.
+//   end      explicit FP64 Rayleigh-Ritz on the nev wanted columns of X with a
+//            complex128 apply; the reported residuals ||A_r y - lambda y|| / lambda
+//            come from it.
 // FAME_FP64: complex128 blocks throughout, explicit FP64 Gram matrices.
 #include <algorithm>
 #include <atomic>
@@ -411,7 +413,8 @@ fame_status rr64(fame_ctx* c, double2* a, double2* aa, double2* b, double2* ab, 
     fame_status s;
     if (do_apply && (s = apply_block<double2>(c, a, aa, m, st)) != FAME_OK) return s;
     const BlockList<double2> U = blocks<double2>(a, m), V = blocks<double2>(aa, m);
-    if ((s = gram_herm<double2>(c, U, V, ld, sm.G, st)) != FAME_OK) return s;
+    // X is a near-eigenbasis here (A X ~ X Theta): the double-float Gram suffices
+    if ((s = gram_herm_df(c, U, V, ld, sm.G, st)) != FAME_OK) return s;
     std::vector<double2> Cm;
     std::vector<double> th;
     // the final FP64 step reduces through the eigen-decomposition of X^H X
@@ -467,13 +470,18 @@ fame_status lob_refine(fame_ctx* c, float2* const S[2], float2* const AS[2], dou
             break;
         }
         if (worst <= 0.5 * tol) {
-            // confirm with a complex128 apply and an explicit FP64 Rayleigh-Ritz
-            std::vector<double> th2 = theta, r2;
-            if ((s = rr64(c, X64[cur], AX64[cur ^ 1], X64[cur ^ 1], AX64[cur], sm, m, true, th2, r2, st)) != FAME_OK) return s;
-            // rr64 left X in X64[cur^1], AX in AX64[cur]: move X back
-            FAME_CUDA_TRY(c, cudaMemcpyAsync(X64[cur], X64[cur ^ 1], (size_t)m * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-            theta = th2;
-            res = r2;
+            // confirm the nev wanted pairs with a complex128 apply and an explicit FP64
+            // Rayleigh-Ritz on their span (a rotation inside span(X[:nev]), which stays
+            // orthogonal to the other columns; those keep their tracked X, AX and theta)
+            const int mc = nev;
+            std::vector<double> th2(theta.begin(), theta.begin() + mc), r2;
+            if ((s = rr64(c, X64[cur], AX64[cur ^ 1], X64[cur ^ 1], AX64[cur], sm, mc, true, th2, r2, st)) != FAME_OK) return s;
+            // rr64 left X in X64[cur^1], AX in AX64[cur] (first mc columns): move X back
+            FAME_CUDA_TRY(c, cudaMemcpyAsync(X64[cur], X64[cur ^ 1], (size_t)mc * ld * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            for (int j = 0; j < mc; ++j) {
+                theta[j] = th2[j];
+                res[j] = r2[j];
+            }
             worst = 0.0;
             for (int j = 0; j < nev; ++j) worst = std::max(worst, res[j]);
             out.theta = theta;

@@ -23,6 +23,14 @@ def _prof():
     }
 
 
+def test_kernel_table_orders_by_time_and_shares_sum_to_one():
+    t = bench.kernel_table(_prof())
+    assert list(t) == ["gram_c64", "xy_c128", "xy_c64", "zin_c64"]
+    assert abs(sum(v["share"] for v in t.values()) - 1.0) < 1e-3
+    assert t["gram_c64"]["launches"] == 4
+    assert abs(t["zin_c64"]["GBps"] - 1.5e9 / 0.5 / 1e6) < 1e-6
+
+
 def test_bound_of_each_kind(monkeypatch):
     monkeypatch.setattr(bench, "measured_peaks", lambda: (6746.0, "measured"))
     P = _prof()
