@@ -60,7 +60,8 @@ def parse():
                     help="pin the complex64 apply plan instead of autotuning it (e.g. for profiling "
                          "runs, where the profiler's overhead would skew the tuning)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the plain-FP64 solve and the band-path batch after the timed steps")
+                    help="skip the plain-FP64 solve, the band-path batch and the gyroid / supercell "
+                         "workloads after the timed steps")
     ap.add_argument("--workload", choices=["fcc64", "tri192"], default="fcc64",
                     help="fcc64 (default): the FCC 64^3 line; tri192: the triclinic 192^3 workload, "
                          "20 bands at each of its 4 Bloch vectors (one step per Bloch vector), mixed "
@@ -412,6 +413,63 @@ def comparisons(ctx, lam_mixed, k_per_lattice=2):
     return res
 
 
+def paper_workloads():
+    """The gyroid of the paper's Section 6 on the BCC lattice at 96^3 with its permittivity
+    swept 3..30 (10 bands at one Bloch vector per permittivity; cold solves, then the sweep
+    again with each permittivity started from the previous one's eigenvectors), and the
+    2 x 2 x 2 simple cubic supercell with a vacancy of Section 7 at 64^3."""
+    import torch
+    from paper_1806_10284_gb300 import fame
+    from paper_1806_10284_gb300 import workloads as W
+    w = W.WORKLOADS["gyroid96"]
+    K = W.bloch_from_reduced(w["vectors"], w["reduced_k"][0])
+    ctx = fame.Context(w["vectors"], w["n"], K)
+    base = W.eps_for("gyroid96", ctx.geometry(), eps_in=2.0)        # mask: 2 inside, 1 outside
+    Bs = [[np.where(b == 2.0, e, 1.0) for b in base] for e in w["eps_sweep"]]
+    ctx.set_eps(*Bs[0])
+    ctx.eigs(w["nev"], tol=w["tol"], flags=fame.FAME_MIXED)      # first-use allocations
+    sweep = []
+    for warm in (False, True):
+        for i, B in enumerate(Bs):
+            ctx.set_eps(*B)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            flags = fame.FAME_MIXED | (fame.FAME_WARM_START if warm and i > 0 else 0)
+            lam, _, it = ctx.eigs(w["nev"], tol=w["tol"], max_iter=800, flags=flags)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if not warm:
+                sweep.append({"eps": w["eps_sweep"][i], "cold_s": dt, "cold_iterations": int(it),
+                              "omega": [float(x) for x in np.sqrt(lam) / (2 * np.pi)], "lam": lam})
+            else:
+                sweep[i].update(warm_s=dt, warm_iterations=int(it),
+                                warm_vs_cold_max_rel=float(np.max(np.abs(lam - sweep[i]["lam"]) / sweep[i]["lam"])))
+    ctx.close()
+    mono = all(np.all(b["lam"] <= a["lam"] * (1 + 1e-7)) for a, b in zip(sweep, sweep[1:]))
+    for r in sweep:
+        del r["lam"]
+    v = W.WORKLOADS["scvac"]
+    Kv = W.bloch_vectors("scvac")[0]
+    cell = fame.geometry_of(fame.plan_lattice(v["vectors"], v["n"], Kv))
+    Vs, ns = W.supercell(v["vectors"], v["n"], v["reps"])
+    c = fame.Context(Vs, ns, Kv)
+    c.set_eps(*W.eps_for("scvac", cell))
+    c.eigs(v["nev"], tol=v["tol"], flags=fame.FAME_MIXED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, _, it = c.eigs(v["nev"], tol=v["tol"], max_iter=800, flags=fame.FAME_MIXED)
+    torch.cuda.synchronize()
+    vac = {"grid": list(ns), "cells": list(v["reps"]), "time_to_10_bands_s": time.perf_counter() - t0,
+           "iterations": int(it), "max_residual": c.stats()["max_residual"],
+           "omega": [float(x) for x in np.sqrt(lam) / (2 * np.pi)]}
+    c.close()
+    torch.cuda.empty_cache()
+    return {"gyroid_eps_sweep": {"grid": list(w["n"]), "level": w["level"], "reduced_k": list(w["reduced_k"][0]),
+                                 "bands": w["nev"], "residual": w["tol"], "bands_fall_with_eps": bool(mono),
+                                 "per_eps": sweep},
+            "vacancy_supercell": vac}
+
+
 def band_paths(k_per_lattice):
     """The band paths in full: per lattice, k_per_lattice Bloch vectors of its path solved
     in one batched mixed call, and three of them again by the plain FP64 solver."""
@@ -612,6 +670,7 @@ def run_ours(args, rank, world, local):
     extras = None
     if world == 1 and not args.no_extras:
         extras = comparisons(ctx, lam)
+        extras["paper_workloads"] = paper_workloads()
     if world == 1 and args.band_path_k > 0:
         extras = dict(extras or {}, band_paths=band_paths(args.band_path_k))
     if rank != 0:

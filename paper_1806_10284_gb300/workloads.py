@@ -197,6 +197,64 @@ def sample_inclusions(geom: Geometry, shapes, eps_in, eps_out=1.0):
     return out
 
 
+def _input_cartesian(geom: Geometry, vectors, X):
+    """Cartesian coordinates, in the frame of the input vectors, of canonical-frame points X
+    (3, ...): fractional coordinates w.r.t. the canonical a1, a2, a3, mapped back to the
+    input vectors (the structure is placed in fractional coordinates of the lattice)."""
+    F = _to_fractional(geom, X)
+    Fin = np.empty_like(F)
+    for l in range(3):
+        Fin[geom.perm[l]] = F[l]
+    return np.tensordot(np.asarray(vectors, dtype=np.float64).T, Fin, axes=(1, 0))
+
+
+def gyroid_value(X):
+    """The gyroid's approximating function sin X cos Y + sin Y cos Z + sin Z cos X,
+    (X, Y, Z) = 2 pi (x, y, z), at Cartesian points (3, ...) in units of the cubic cell."""
+    x, y, z = (2.0 * math.pi * X[i] for i in range(3))
+    return np.sin(x) * np.cos(y) + np.sin(y) * np.cos(z) + np.sin(z) * np.cos(x)
+
+
+def sample_level_set(geom: Geometry, vectors, fn, level, eps_in, eps_out=1.0):
+    """B_1, B_2, B_3 with eps_in at the Yee points where fn(X) > level, X Cartesian in the
+    frame of the input vectors, and eps_out elsewhere."""
+    out = []
+    n1, n2, n3 = geom.n
+    slab = max(1, (1 << 18) // (n1 * n2))
+    for comp in range(3):
+        B = np.empty(geom.shape, dtype=np.float64)
+        for k0 in range(0, n3, slab):
+            k1 = min(n3, k0 + slab)
+            X = _input_cartesian(geom, vectors, yee_points(geom, comp, k0, k1))
+            B[k0:k1] = np.where(fn(X) > level, eps_in, eps_out)
+        out.append(B)
+    return out
+
+
+def supercell(vectors, n, reps):
+    """Primitive vectors (rows N_l a_l) and grid (N_l n_l) of the supercell of reps =
+    (N_1, N_2, N_3) primitive cells.  Grid sizes and reps follow the canonical axes,
+    so the helper serves lattices whose canonical order is the input order in both
+    cells (e.g. simple cubic, N_1 >= N_2 >= N_3)."""
+    V = np.asarray(vectors, dtype=np.float64)
+    return V * np.asarray(reps, dtype=np.float64)[:, None], tuple(int(a) * int(b) for a, b in zip(n, reps))
+
+
+def tile_eps(B, reps, empty_cells=(), eps_out=1.0):
+    """The primitive-cell B_1, B_2, B_3 (each (n3, n2, n1)) repeated reps = (N_1, N_2, N_3)
+    times; each primitive cell (i, j, k) in ``empty_cells`` is set to eps_out (a vacancy:
+    the inclusions of that cell removed)."""
+    N1, N2, N3 = reps
+    out = []
+    for b in B:
+        n3, n2, n1 = b.shape
+        t = np.tile(b, (N3, N2, N1))
+        for (i, j, k) in empty_cells:
+            t[k * n3:(k + 1) * n3, j * n2:(j + 1) * n2, i * n1:(i + 1) * n1] = eps_out
+        out.append(t)
+    return out
+
+
 def smooth_field_eps(n, seed, sigma_vox=3.0, contrast=12.0, steep=8.0):
     """eps on grid nodes: 1 + contrast * sigmoid(steep * g), g a Gaussian-filtered
     (sigma in voxels, periodic) unit-variance white-noise field; then B_l at
@@ -281,7 +339,7 @@ def random_block(seed, n, m, dtype=np.complex128):
 
 
 # ---------------------------------------------------------------------------
-# The five workloads.
+# The workloads.
 # ---------------------------------------------------------------------------
 
 WORKLOADS = {
@@ -315,6 +373,18 @@ WORKLOADS = {
                           "objective (lambda6-lambda5)/lambda5",
                      vectors=simple_cubic(), n=(48, 48, 48), kseed=404, nk=8, seed=401,
                      nev=6, tol=1e-8, precision="mixed"),
+    "gyroid96": dict(desc="BCC a=1, 96^3, gyroid sin X cos Y + sin Y cos Z + sin Z cos X > 1.1 "
+                          "filled with eps (13; the sweep takes 3..30), 10 bands",
+                     vectors=bcc(), n=(96, 96, 96), level=1.1, eps_in=13.0,
+                     eps_sweep=(3.0, 5.0, 8.0, 13.0, 18.0, 24.0, 30.0),
+                     reduced_k=[np.array([0.5, 0.5, 0.0]), np.array([0.25, 0.25, 0.25])],
+                     nev=10, tol=1e-8, precision="mixed"),
+    "scvac": dict(desc="simple cubic supercell of 2 x 2 x 2 cells (64^3), eps=13 sphere r=0.25 "
+                       "per cell, one cell's sphere removed (a vacancy), 10 bands",
+                  vectors=simple_cubic(), n=(32, 32, 32), reps=(2, 2, 2), vacancy=[(0, 0, 0)],
+                  shapes=[dict(kind="sphere", center=np.array([0.5, 0.5, 0.5]), radius=0.25)],
+                  bloch=[np.pi * np.array([0.5, 0.1, 0.2])],
+                  eps_in=13.0, nev=10, tol=1e-8, precision="mixed"),
     "tri192": dict(desc="triclinic |a|=1,1.1,1.25, angles 80/85/95 deg, 192^3, 8 seeded "
                         "ellipsoids eps=13, 20 bands at 4 k-points",
                    vectors=triclinic(1.0, 1.1, 1.25, 80.0, 85.0, 95.0), n=(192, 192, 192),
@@ -336,15 +406,22 @@ def bloch_vectors(name):
             for c in random_reduced_kpoints(w["kseed"], w["nk"])]
 
 
-def eps_for(name, geom: Geometry):
-    """B_1, B_2, B_3 for a workload on the supplied grid geometry."""
+def eps_for(name, geom: Geometry, eps_in=None):
+    """B_1, B_2, B_3 for a workload on the supplied grid geometry (for the supercell
+    workload: the geometry of its primitive cell; the result is the tiled supercell).
+    ``eps_in`` overrides the workload's inclusion permittivity (the eps sweep)."""
     w = WORKLOADS[name]
+    e_in = w.get("eps_in") if eps_in is None else eps_in
     if name == "sc48grad":
         return smooth_field_eps(geom.n, w["seed"])[1]
+    if "level" in w:
+        return sample_level_set(geom, w["vectors"], gyroid_value, w["level"], e_in)
+    if "reps" in w:
+        return tile_eps(sample_inclusions(geom, w["shapes"], e_in), w["reps"], w["vacancy"])
     if "shapes" in w:
         shapes = w["shapes"]
     elif name == "tri192":
         shapes = random_ellipsoids(w["seed"])
     else:
         shapes = random_inclusions(w["seed"], w["vectors"])
-    return sample_inclusions(geom, shapes, w["eps_in"])
+    return sample_inclusions(geom, shapes, e_in)
