@@ -672,6 +672,9 @@ __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(Bl
     // as (re h, re l, im h, im l), and the block table [mo][kRefBlk + 1]
     float4* cfd = reinterpret_cast<float4*>(ps + ((k + 1) & ~1));
     int* blk = reinterpret_cast<int*>(cfd + (RF ? mo * kRefBlk : 0));
+    // refinement form: the tile's rows of the complex128 X, [mx][kStRows], copied when the
+    // tile starts so that the epilogue finds them in shared memory
+    double2* xs = reinterpret_cast<double2*>(blk + (RF ? mo * (kRefBlk + 1) : 0));
     if constexpr (RF) {
         for (int e = tid; e < mo * (kRefBlk + 1); e += nthr) {
             const int j = e / (kRefBlk + 1);
@@ -736,6 +739,18 @@ __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(Bl
     int c_buf = 0;
     for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const size_t row = tile * kStRows + rl;
+        if constexpr (RF) {
+            // one more copy group, older than the tile's nchunk stages: complete by the
+            // last chunk's wait when nchunk >= kStStages - 1, else waited for below
+            __syncthreads();                                   // the previous epilogue has read xs
+            const size_t rbase = tile * kStRows;
+            for (int e = tid; e < rf.mx * kStRows; e += nthr) {
+                const int i = e / kStRows, r = e - i * kStRows;
+                const bool ok = rbase + r < ld;
+                cp_async16(xs + e, ok ? rf.X64 + (size_t)i * ld + rbase + r : rf.X64, ok);
+            }
+            cp_async_commit();
+        }
         float2 acc[kStOut];
 #pragma unroll
         for (int j = 0; j < kStOut; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -768,6 +783,14 @@ __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(Bl
             c_buf = c_buf + 1 == kStStages ? 0 : c_buf + 1;
             __syncthreads();
         }
+        if constexpr (RF) {
+            static_assert(kStStages == 4, "the waits below cover nchunk < kStStages - 1");
+            if (nchunk < kStStages - 1) {
+                if (nchunk == 1) cp_async_wait<1>();
+                else cp_async_wait<2>();
+                __syncthreads();
+            }
+        }
         if (row < ld) {
 #pragma unroll
             for (int j = 0; j < kStOut; ++j) {
@@ -785,7 +808,7 @@ __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(Bl
                     const int* b = blk + jj * (kRefBlk + 1);
                     float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f;
                     for (int t = 0; t < b[0]; ++t) {
-                        const double2 x = rf.X64[(size_t)b[1 + t] * ld + row];
+                        const double2 x = xs[b[1 + t] * kStRows + rl];
                         const df64::Split xr = df64::split(x.x), xi = df64::split(x.y);
                         const float4 w = cfd[jj * kRefBlk + t];
                         df64::mac(Sr, Er, xr.h, xr.l, w.x, w.y);
@@ -917,7 +940,9 @@ size_t combine_st_smem(int k, int groups, bool refine = false) {
     const int kp = (k + kStCols - 1) / kStCols * kStCols;
     return (size_t)kp * groups * kStOut * sizeof(float2) +
            (size_t)kStStages * kStCols * kStRows * sizeof(float2) + (size_t)((k + 1) & ~1) * sizeof(void*) +
-           (refine ? (size_t)groups * kStOut * (kRefBlk * sizeof(float4) + (kRefBlk + 1) * sizeof(int)) : 0);
+           (refine ? (size_t)groups * kStOut *
+                         (kRefBlk * sizeof(float4) + (kRefBlk + 1) * sizeof(int) + kStRows * sizeof(double2))
+                   : 0);
 }
 
 // R_j = AX_j - theta_j X_j;  W_j = tinv .* R_j (tinv indexed by frequency, both coordinates);
