@@ -264,7 +264,7 @@ FFT_PASSES = ("zin", "xy", "zout", "ypass", "xpass")
 
 
 KERNEL_SOURCES = ("apply3.cu", "blockops.cu", "transforms.cu", "eps.cu", "noalloc.cu", "tc_gram.cu", "precond.cu", "lanczos.cu", "tc.cuh", "fft2.cuh",
-                  "phases.cuh", "df64.cuh", "fame_internal.h", "blockops.h")
+                  "phases.cuh", "df64.cuh", "dfloat.cuh", "fame_internal.h", "blockops.h")
 
 
 def kernel_source_hash():
@@ -295,13 +295,14 @@ def _bound(name, st):
     passes are HBM bound (the pass model); every other kernel is HBM bound when its
     algorithmic intensity (flops per algorithmic byte) lies below the ridge of the
     arithmetic units it runs on (FP32 lanes for complex64 work and for the double-float
-    update, FP64 units for complex128 work), else bound by those units."""
+    kinds "*_df": the refinement update and the complex128 passes in double-float
+    arithmetic; FP64 units for the other complex128 work), else bound by those units."""
     base, prec = name.rsplit("_", 1)
     hbm, kind = measured_peaks()
     hbm_src = (f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else "fallback 6.8 TB/s")
     if base in FFT_PASSES and prec == "c64":
         return "hbm", hbm, "GB/s", hbm_src
-    if prec == "c128" and base != "combine_df":
+    if prec == "c128" and not base.endswith("_df"):
         alu, alu_src = FP64_PEAK_TFLOPS, "nominal FP64 rate (recipe table)"
     else:
         alu, alu_src = FP32_PEAK_TFLOPS, "FP32 lanes x clock (recipe table: 152 SMs, 2.07 GHz)"

@@ -61,8 +61,15 @@ typedef enum {
                          /* (limit: environment FAME_WAIT_TIMEOUT_MS, default 1000)      */
 } fame_status;
 
-/* dtype of vectors passed to fame_apply_Ar / fame_lift */
-enum { FAME_C64 = 0, FAME_C128 = 1 };
+/* dtype of vectors passed to fame_apply_Ar / fame_lift.  FAME_C128_DF: complex128
+ * vectors (the same memory layout as FAME_C128), transformed in double-float
+ * arithmetic -- pairs of floats, about 48 significant bits -- on the FP32 units,
+ * which on GB300 run FP64 work at 1/64 of their rate; results agree with FAME_C128
+ * to about 1e-14 of the largest entry.  Grids whose x-y plane does not fit in
+ * shared memory (the split y / x / y passes) take the FAME_C128 path instead.
+ * The eigensolver uses this form for its complex128 applies when the requested
+ * residual is at least 1e-10 (environment FAME_FP64_NATIVE=1: never). */
+enum { FAME_C64 = 0, FAME_C128 = 1, FAME_C128_DF = 2 };
 
 /* flags of fame_eigs */
 enum {
@@ -155,7 +162,7 @@ FAME_API fame_status fame_set_eps_device(fame_ctx* ctx, const double* B, void* s
  * (SVD).
  *   y, Ay : device, [m][2][n] complex of type dtype; may not overlap.
  *   m     : number of vectors, 1 <= m <= 4096.
- *   dtype : FAME_C64 or FAME_C128.
+ *   dtype : FAME_C64, FAME_C128 or FAME_C128_DF.
  * Asynchronous on stream.  Errors: FAME_E_ARG, FAME_E_STATE (no eps set),
  * FAME_E_NOMEM (workspace), FAME_E_CUDA.
  */

@@ -243,9 +243,10 @@ fame_status fame_apply_Ar(fame_ctx* c, const void* y, void* Ay, int m, int dtype
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (dtype == FAME_C64)
         return run_apply<float>(c, static_cast<const float2*>(y), static_cast<float2*>(Ay), m, st);
-    if (dtype == FAME_C128)
-        return run_apply<double>(c, static_cast<const double2*>(y), static_cast<double2*>(Ay), m, st);
-    return set_err(c, FAME_E_ARG, "dtype must be FAME_C64 or FAME_C128");
+    if (dtype == FAME_C128 || dtype == FAME_C128_DF)
+        return run_apply_c128(c, static_cast<const double2*>(y), static_cast<double2*>(Ay), m,
+                              dtype == FAME_C128_DF, st);
+    return set_err(c, FAME_E_ARG, "dtype must be FAME_C64, FAME_C128 or FAME_C128_DF");
 }
 
 fame_status fame_lift(fame_ctx* c, const void* y, void* x, int m, int dtype, void* stream) {
@@ -255,9 +256,10 @@ fame_status fame_lift(fame_ctx* c, const void* y, void* x, int m, int dtype, voi
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (dtype == FAME_C64)
         return run_lift<float>(c, static_cast<const float2*>(y), static_cast<float2*>(x), m, st);
-    if (dtype == FAME_C128)
-        return run_lift<double>(c, static_cast<const double2*>(y), static_cast<double2*>(x), m, st);
-    return set_err(c, FAME_E_ARG, "dtype must be FAME_C64 or FAME_C128");
+    if (dtype == FAME_C128 || dtype == FAME_C128_DF)
+        return run_lift_c128(c, static_cast<const double2*>(y), static_cast<double2*>(x), m,
+                             dtype == FAME_C128_DF, st);
+    return set_err(c, FAME_E_ARG, "dtype must be FAME_C64, FAME_C128 or FAME_C128_DF");
 }
 
 fame_status fame_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, double* lambda_out,

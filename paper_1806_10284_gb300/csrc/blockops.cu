@@ -12,14 +12,14 @@
 #include "blockops.h"
 #include "df64.cuh"
 
-namespace {
-
 // FP64 arithmetic on the FP64 units instead of double-float on the FP32 units (the
 // environment variable FAME_FP64_NATIVE=1; for comparisons)
 bool fp64_native() {
     const char* v = std::getenv("FAME_FP64_NATIVE");
     return v && v[0] == '1';
 }
+
+namespace {
 
 // Complex64 Grams whose wider side has at least this many vectors run on the tensor
 // cores (tc_gram.cu); narrower ones on the FP32 ring kernel, which is faster there

@@ -139,6 +139,8 @@ struct fame_ctx {
     DevTables<double> td;
     uint32_t* alt_mask = nullptr;  // reference-vector decision per frequency (FP64)
     bool eps_set = false;
+    // complex128 applies of the current solve in double-float arithmetic (set per solve)
+    bool df128 = false;
     double mean_invB = 0.0;
     double min_invB = 0.0, max_invB = 0.0;   // spectrum bounds of Q_r^* B^{-1} Q_r
     GrowBuf cheb;                  // Chebyshev preconditioner blocks (complex64)
@@ -177,7 +179,8 @@ void count_launch(int k = 1);
 
 // kernel kinds for the opt-in profiler (profile.cpp)
 enum KernelKind { K_ZIN, K_XY, K_ZOUT, K_YPASS, K_XPASS, K_GRAM, K_GRAM_RED, K_COMBINE, K_RESID,
-                  K_CONVERT, K_GRAD, K_SETUP, K_GRAM_HERM, K_ORTH, K_COMBINE_DF, K_PRECOND, K_COUNT };
+                  K_CONVERT, K_GRAD, K_SETUP, K_GRAM_HERM, K_ORTH, K_COMBINE_DF, K_PRECOND,
+                  K_ZIN_DF, K_XY_DF, K_ZOUT_DF, K_COUNT };
 // Brackets a launch with events on its stream when profiling is on; attaches the
 // launch's algorithmic bytes and flops.
 // NVTX range on the calling host thread (header-only NVTX 3: a no-op branch unless a
@@ -224,6 +227,13 @@ fame_status run_apply_into(fame_ctx* c, const typename cpx<R>::T* y, typename cp
 template <typename R>
 fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::T* x, int m,
                      cudaStream_t st);
+// complex128 apply / lift; with df (and where the two-level passes cover the grid) in
+// double-float arithmetic on the FP32 units, else in FP64
+bool c128_df_available(const fame_ctx* c, int m);
+fame_status run_apply_c128(fame_ctx* c, const double2* y, double2* Ay, int m, bool df, cudaStream_t st);
+fame_status run_lift_c128(fame_ctx* c, const double2* y, double2* x, int m, bool df, cudaStream_t st);
+// FP64 arithmetic forced for every complex128 step (environment FAME_FP64_NATIVE=1)
+bool fp64_native();
 // E = B^{-1} Q_r Sigma_r y and H = -i sqrt(lambda) P_r y for m eigenpairs (complex128)
 fame_status run_fields(fame_ctx* c, const double2* y, const double* lambda, double2* E, double2* H, int m,
                        cudaStream_t st);

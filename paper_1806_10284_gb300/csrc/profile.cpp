@@ -44,7 +44,7 @@ Prof& prof() {
 
 const char* kNames[K_COUNT] = {"zin", "xy", "zout", "ypass", "xpass", "gram", "gram_reduce",
                                "combine", "resid", "convert", "grad_accum", "setup", "gram_herm",
-                               "orth", "combine_df", "precond"};
+                               "orth", "combine_df", "precond", "zin_df", "xy_df", "zout_df"};
 
 // "zin_c64", "zin_c128", ... in the order of the profiler's ids
 struct RangeNames {

@@ -59,8 +59,14 @@ fame_status apply_block<float2>(fame_ctx* c, const float2* y, float2* Ay, int m,
 template <>
 fame_status apply_block<double2>(fame_ctx* c, const double2* y, double2* Ay, int m, cudaStream_t st) {
     c->stats.applies_c128 += m;
-    return run_apply<double>(c, y, Ay, m, st);
+    return run_apply_c128(c, y, Ay, m, c->df128, st);
 }
+
+// Requested residuals of at least this size take the complex128 applies in
+// double-float arithmetic: their rounding, about 2^-47 relative per operation and
+// amplified by roughly sqrt(||A_r|| / lambda) through Sigma_r at both ends, stays
+// one to two orders of magnitude below the residual up to 192^3 grids.
+constexpr double kDf128MinTol = 1e-10;
 
 template <typename R>
 const R* tinv_of(const fame_ctx* c);
@@ -555,6 +561,7 @@ fame_status run_eigs(fame_ctx* c, int nev, double tol, int max_iter, int flags, 
     const bool mixed = (flags & FAME_MIXED) && !(flags & FAME_FP64);
     c->stats = fame_solve_stats{};
     c->stats_rr_ms = 0.0;
+    c->df128 = !fp64_native() && tol >= kDf128MinTol;
     fame_status s;
     if ((s = tc_reset_err(c, st)) != FAME_OK) return s;
     const int k = 3 * m;

@@ -24,8 +24,33 @@
 #include <vector>
 
 #include "fame_internal.h"
+#include "dfloat.cuh"
 #include "fft2.cuh"
 #include "phases.cuh"
+
+// double-float complex arithmetic over complex128 storage (dfloat.cuh)
+template <> struct cpx<dfr> { using T = dfc; };
+
+namespace {
+// The two-level kernels below take the arithmetic complex type A as a template
+// argument: the storage type itself (float2, double2), or dfc over complex128
+// storage, converted at every global load and store.
+template <typename A, typename C>
+__device__ __forceinline__ A as_arith(const C& v) {
+    if constexpr (std::is_same<A, C>::value) return v;
+    else return to_df(v);
+}
+template <typename C, typename A>
+__device__ __forceinline__ C as_store(const A& v) {
+    if constexpr (std::is_same<A, C>::value) return v;
+    else return to_double(v);
+}
+template <typename Ar, typename R>
+__device__ __forceinline__ Ar as_arith_r(R v) {
+    if constexpr (std::is_same<Ar, R>::value) return v;
+    else return to_df(v);
+}
+}  // namespace
 
 namespace {
 // ---------------------------------------------------------------------------
@@ -530,28 +555,28 @@ __global__ void k_precond(KParams<R> P, R* __restrict__ tinv, R mean_invB) {
 // q / d for 0 <= q < 2^20, d <= 1024, via a float reciprocal (exact in that range)
 __device__ __forceinline__ int fdiv(int q, float inv_d) { return __float2int_rz(((float)q + 0.5f) * inv_d); }
 
-template <typename R>
+template <typename R, typename A = typename cpx<R>::T>
 __global__ void __launch_bounds__(512) k_zin2(KParams<R> P, const typename cpx<R>::T* __restrict__ y,
-                                              typename cpx<R>::T* __restrict__ W, int m, int lgTP,
-                                              int vpc) {
+                                              A* __restrict__ W, int m, int lgTP, int vpc) {
     using C = typename cpx<R>::T;
+    using Ar = decltype(A().x);
     using F = typename FracT<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
     const int TP = 1 << lgTP, NP = 3 * TP;
     const size_t n = (size_t)n1 * n2 * n3;
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    C* L0s = tw + n3;
-    C* L1s = L0s + TP;
+    A* tw = reinterpret_cast<A*>(smem_raw);
+    A* L0s = tw + n3;
+    A* L1s = L0s + TP;
     F* F3s = reinterpret_cast<F*>(L1s + TP);
-    C* X = L1s + 2 * TP;                 // F3s occupies TP entries of C size
-    C* Y = X + (size_t)n3 * NP;
+    A* X = L1s + 2 * TP;                 // F3s occupies TP entries of A size
+    A* Y = X + (size_t)n3 * NP;
     const int q = blockIdx.y, p0 = blockIdx.x * TP;
-    load_table(tw, P.tw[2], n3);
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = as_arith<A>(P.tw[2][i]);
     for (int pp = threadIdx.x; pp < TP; pp += blockDim.x) {
         const int p = min(p0 + pp, n1 - 1);
-        L0s[pp] = lambda_of(p, n1, P.f1, P.inv_dx);
-        L1s[pp] = lambda_of(q, n2, P.f2[p], P.inv_dy);
+        L0s[pp] = as_arith<A>(lambda_of(p, n1, P.f1, P.inv_dx));
+        L1s[pp] = as_arith<A>(lambda_of(q, n2, P.f2[p], P.inv_dy));
         F3s[pp] = P.f3[(size_t)q * n1 + p];
     }
     __syncthreads();
@@ -561,83 +586,87 @@ __global__ void __launch_bounds__(512) k_zin2(KParams<R> P, const typename cpx<R
         const C* yv = y + (size_t)v * 2 * n;
         for (int e = threadIdx.x; e < tile; e += blockDim.x) {
             const int r = e >> lgTP, pp = e & (TP - 1), p = p0 + pp;
-            C o0 = mk((R)0, (R)0), o1 = o0, o2 = o0;
+            A o0 = mk((Ar)0, (Ar)0), o1 = o0, o2 = o0;
             if (p < n1) {
                 const size_t f = ((size_t)r * n2 + q) * n1 + p;
-                const C y1 = yv[f], y2 = yv[n + f];
-                const C L0 = L0s[pp], L1 = L1s[pp];
-                const PencilBasis<R> pb{L0, L1, L0 + L1, L0 - L1,
-                                        L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y};
-                expand<R>(pb, P.lam3[f], alt_bit(P.alt, f), y1, y2, o0, o1, o2);
-                if (P.curl) curl_of(L0, L1, P.lam3[f], o0, o1, o2);
+                const A y1 = as_arith<A>(yv[f]), y2 = as_arith<A>(yv[n + f]);
+                const A L0 = L0s[pp], L1 = L1s[pp];
+                const PencilBasis<Ar> pb{L0, L1, L0 + L1, L0 - L1,
+                                         L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y};
+                expand<Ar>(pb, as_arith<A>(P.lam3[f]), alt_bit(P.alt, f), y1, y2, o0, o1, o2);
+                if constexpr (std::is_same<A, C>::value) {
+                    if (P.curl) curl_of(L0, L1, P.lam3[f], o0, o1, o2);
+                }
             }
             X[r * NP + pp] = o0;
             X[r * NP + TP + pp] = o1;
             X[r * NP + 2 * TP + pp] = o2;
         }
         __syncthreads();
-        C* Wv = W + (size_t)v * 3 * n;
+        A* Wv = W + (size_t)v * 3 * n;
         fft2::pencils_any<true>(
             n3, NP, tw, Y, [&](int pc, int e) { return X[e * NP + pc]; },
-            [&](int pc, int c, C val) {
+            [&](int pc, int c, A val) {
                 const int l = pc >> lgTP, pp = pc & (TP - 1), p = p0 + pp;
                 if (p < n1)
-                    Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p] = cmul(val, P.tw3[((size_t)c * n2 + q) * n1 + p]);
+                    Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p] =
+                        cmul(val, as_arith<A>(P.tw3[((size_t)c * n2 + q) * n1 + p]));
             });
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(512) k_zout2(KParams<R> P, const typename cpx<R>::T* __restrict__ W,
+template <typename R, typename A = typename cpx<R>::T>
+__global__ void __launch_bounds__(512) k_zout2(KParams<R> P, const A* __restrict__ W,
                                                typename cpx<R>::T* __restrict__ out, int m, int lgTP,
                                                int vpc) {
     using C = typename cpx<R>::T;
+    using Ar = decltype(A().x);
     using F = typename FracT<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
     const int TP = 1 << lgTP, NP = 3 * TP;
     const size_t n = (size_t)n1 * n2 * n3;
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    C* L0s = tw + n3;
-    C* L1s = L0s + TP;
+    A* tw = reinterpret_cast<A*>(smem_raw);
+    A* L0s = tw + n3;
+    A* L1s = L0s + TP;
     F* F3s = reinterpret_cast<F*>(L1s + TP);
-    C* X = L1s + 2 * TP;
-    C* Y = X + (size_t)n3 * NP;
+    A* X = L1s + 2 * TP;
+    A* Y = X + (size_t)n3 * NP;
     const int q = blockIdx.y, p0 = blockIdx.x * TP;
-    load_table(tw, P.tw[2], n3);
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = as_arith<A>(P.tw[2][i]);
     for (int pp = threadIdx.x; pp < TP; pp += blockDim.x) {
         const int p = min(p0 + pp, n1 - 1);
-        L0s[pp] = lambda_of(p, n1, P.f1, P.inv_dx);
-        L1s[pp] = lambda_of(q, n2, P.f2[p], P.inv_dy);
+        L0s[pp] = as_arith<A>(lambda_of(p, n1, P.f1, P.inv_dx));
+        L1s[pp] = as_arith<A>(lambda_of(q, n2, P.f2[p], P.inv_dy));
         F3s[pp] = P.f3[(size_t)q * n1 + p];
     }
     __syncthreads();
     const int tile = n3 * TP;
     const int v1 = min(m, (int)(blockIdx.z + 1) * vpc);
     for (int v = blockIdx.z * vpc; v < v1; ++v) {
-        const C* Wv = W + (size_t)v * 3 * n;
+        const A* Wv = W + (size_t)v * 3 * n;
         fft2::pencils_any<false>(
             n3, NP, tw, Y,
             [&](int pc, int c) {
                 const int l = pc >> lgTP, pp = pc & (TP - 1), p = p0 + pp;
-                if (p >= n1) return mk((R)0, (R)0);
-                const C x = Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p];
-                return cmulc(P.tw3[((size_t)c * n2 + q) * n1 + p], x);
+                if (p >= n1) return mk((Ar)0, (Ar)0);
+                const A x = Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p];
+                return cmulc(as_arith<A>(P.tw3[((size_t)c * n2 + q) * n1 + p]), x);
             },
-            [&](int pc, int r, C val) { X[r * NP + pc] = val; });
+            [&](int pc, int r, A val) { X[r * NP + pc] = val; });
         C* ov = out + (size_t)v * 2 * n;
         for (int e = threadIdx.x; e < tile; e += blockDim.x) {
             const int r = e >> lgTP, pp = e & (TP - 1), p = p0 + pp;
             if (p < n1) {
                 const size_t f = ((size_t)r * n2 + q) * n1 + p;
-                const C L0 = L0s[pp], L1 = L1s[pp];
-                const PencilBasis<R> pb{L0, L1, L0 + L1, L0 - L1,
-                                        L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y};
-                C z1, z2;
-                contract<R>(pb, P.lam3[f], alt_bit(P.alt, f), X[r * NP + pp], X[r * NP + TP + pp],
-                            X[r * NP + 2 * TP + pp], z1, z2);
-                ov[f] = z1;
-                ov[n + f] = z2;
+                const A L0 = L0s[pp], L1 = L1s[pp];
+                const PencilBasis<Ar> pb{L0, L1, L0 + L1, L0 - L1,
+                                         L0.x * L0.x + L0.y * L0.y + L1.x * L1.x + L1.y * L1.y};
+                A z1, z2;
+                contract<Ar>(pb, as_arith<A>(P.lam3[f]), alt_bit(P.alt, f), X[r * NP + pp], X[r * NP + TP + pp],
+                             X[r * NP + 2 * TP + pp], z1, z2);
+                ov[f] = as_store<C>(z1);
+                ov[n + f] = as_store<C>(z2);
             }
         }
         __syncthreads();
@@ -645,26 +674,28 @@ __global__ void __launch_bounds__(512) k_zout2(KParams<R> P, const typename cpx<
 }
 
 // One z-plane per block; plane kept with row stride n1 + 1.
-template <typename R>
-__global__ void __launch_bounds__(512) k_xy2(KParams<R> P, typename cpx<R>::T* __restrict__ W, int mode,
-                                             R lift_scale) {
+// With A the double-float type, W holds double-float values on entry; mode 0 leaves
+// double-float values, modes 1 and 2 (the lift's last pass) write complex128.
+template <typename R, typename A = typename cpx<R>::T>
+__global__ void __launch_bounds__(512) k_xy2(KParams<R> P, A* __restrict__ W, int mode, R lift_scale) {
     using C = typename cpx<R>::T;
+    using Ar = decltype(A().x);
     using F = typename FracT<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
     const int np = n1 * n2, S = n1 + 1;
-    C* twx = reinterpret_cast<C*>(smem_raw);
-    C* twy = twx + n1;
+    A* twx = reinterpret_cast<A*>(smem_raw);
+    A* twy = twx + n1;
     F* F2s = reinterpret_cast<F*>(twy + n2);
-    C* X = twy + n2 + n1;                // F2s occupies n1 entries of C size
-    C* Y = X + (size_t)n2 * S;
+    A* X = twy + n2 + n1;                // F2s occupies n1 entries of A size
+    A* Y = X + (size_t)n2 * S;
     const int plane = blockIdx.x;
     const int c = plane % n3;
     const int l = (plane / n3) % 3;
-    C* g = W + (size_t)plane * np;
+    A* g = W + (size_t)plane * np;
     const float inv_n1 = 1.0f / (float)n1;
-    load_table(twx, P.tw[0], n1);
-    load_table(twy, P.tw[1], n2);
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) twx[i] = as_arith<A>(P.tw[0][i]);
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) twy[i] = as_arith<A>(P.tw[1][i]);
     for (int p = threadIdx.x; p < n1; p += blockDim.x) F2s[p] = P.f2[p];
     for (int e = threadIdx.x; e < np; e += blockDim.x) {
         const int b = fdiv(e, inv_n1), a = e - b * n1;
@@ -674,33 +705,38 @@ __global__ void __launch_bounds__(512) k_xy2(KParams<R> P, typename cpx<R>::T* _
     // inverse y-DFT over columns, then D_a2
     fft2::pencils_any<true>(
         n2, n1, twy, Y, [&](int p, int b) { return X[b * S + p]; },
-        [&](int p, int b, C v) { X[b * S + p] = cmul(v, P.tw2[b * n1 + p]); });
+        [&](int p, int b, A v) { X[b * S + p] = cmul(v, as_arith<A>(P.tw2[b * n1 + p])); });
     // inverse x-DFT over rows
     fft2::pencils_any<true>(
         n1, n2, twx, Y, [&](int b, int a) { return X[b * S + a]; },
-        [&](int b, int a, C v) { X[b * S + a] = v; });
+        [&](int b, int a, A v) { X[b * S + a] = v; });
     const R* ib = P.invB + (size_t)l * n3 * np + (size_t)c * np;
     if (mode == 0) {
+        const Ar sc = as_arith_r<Ar>(P.scale);
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int b = fdiv(e, inv_n1), a = e - b * n1;
-            X[b * S + a] = (ib[e] * P.scale) * X[b * S + a];
+            X[b * S + a] = (as_arith_r<Ar>(ib[e]) * sc) * X[b * S + a];
         }
         __syncthreads();
         fft2::pencils_any<false>(
             n1, n2, twx, Y, [&](int b, int a) { return X[b * S + a]; },
-            [&](int b, int a, C v) { X[b * S + a] = v; });
+            [&](int b, int a, A v) { X[b * S + a] = v; });
         fft2::pencils_any<false>(
             n2, n1, twy, Y,
-            [&](int p, int b) { return cmulc(P.tw2[b * n1 + p], X[b * S + p]); },
-            [&](int p, int b, C v) { X[b * S + p] = v; });
+            [&](int p, int b) { return cmulc(as_arith<A>(P.tw2[b * n1 + p]), X[b * S + p]); },
+            [&](int p, int b, A v) { X[b * S + p] = v; });
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int b = fdiv(e, inv_n1), a = e - b * n1;
             g[e] = X[b * S + a];
         }
     } else {
+        // the complex128 result goes over the double-float input in place (same size)
+        C* gc = reinterpret_cast<C*>(g);
+        const Ar ls = as_arith_r<Ar>(lift_scale);
         for (int e = threadIdx.x; e < np; e += blockDim.x) {
             const int b = fdiv(e, inv_n1), a = e - b * n1;
-            g[e] = (mode == 2 ? lift_scale : ib[e] * lift_scale) * cmul(X[b * S + a], P.tw1[a]);
+            const Ar s = mode == 2 ? ls : as_arith_r<Ar>(ib[e]) * ls;
+            gc[e] = as_store<C>(s * cmul(X[b * S + a], as_arith<A>(P.tw1[a])));
         }
     }
 }
@@ -975,6 +1011,81 @@ fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::
     return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
 }
 
+// ---------------------------------------------------------------------------
+// Complex128 apply and lift in double-float arithmetic: the two-level passes with
+// A = dfc.  y, Ay and the lift's output are complex128; the workspace between the
+// passes holds double-float values (the same 16 bytes per complex entry).
+// ---------------------------------------------------------------------------
+bool c128_df_available(const fame_ctx* c, int m) {
+    const int n1 = c->plan.n[0], n2 = c->plan.n[1];
+    return z2_config<double>(c, m).ok && fft2::supported(n1) && fft2::supported(n2) &&
+           xy2_smem<double>(n1, n2) <= kSmemCap;
+}
+
+static fame_status z_pass_df(fame_ctx* c, const KParams<double>& P, const double2* y, dfc* W,
+                             const dfc* Wz, double2* out, int m, bool zin, cudaStream_t st) {
+    const Z2Cfg z2 = z2_config<double>(c, m);
+    const void* fn = zin ? (const void*)k_zin2<double, dfc> : (const void*)k_zout2<double, dfc>;
+    fame_status s = set_smem<double>(c, fn, z2.smem);
+    if (s != FAME_OK) return s;
+    const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2], TP = 1 << z2.lgTP;
+    const double nm = (double)c->n * m;
+    dim3 grid((n1 + TP - 1) / TP, n2, (m + z2.vpc - 1) / z2.vpc);
+    {
+        ProfScope ps(zin ? K_ZIN_DF : K_ZOUT_DF, true, st, 5.0 * nm * sizeof(double2),
+                     3 * nm * 5.0 * lg2(n3) + 60.0 * nm);
+        if (zin)
+            k_zin2<double, dfc><<<grid, z2.threads, z2.smem, st>>>(P, y, W, m, z2.lgTP, z2.vpc);
+        else
+            k_zout2<double, dfc><<<grid, z2.threads, z2.smem, st>>>(P, Wz, out, m, z2.lgTP, z2.vpc);
+    }
+    count_launch();
+    FAME_CUDA_TRY(c, cudaGetLastError());
+    return FAME_OK;
+}
+
+static fame_status xy_df(fame_ctx* c, const KParams<double>& P, dfc* W, int m, int mode, double lift_scale,
+                         cudaStream_t st) {
+    const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
+    const size_t smem2 = xy2_smem<double>(n1, n2);
+    fame_status s = set_smem<double>(c, (const void*)k_xy2<double, dfc>, smem2);
+    if (s != FAME_OK) return s;
+    const fft2::Split sx = fft2::split_of(n1), sy = fft2::split_of(n2);
+    const int work = std::max(n1 * std::max(sy.R1, sy.R2), n2 * std::max(sx.R1, sx.R2));
+    const int th = std::min(512, std::max(128, ((work + 31) / 32) * 32));
+    const double nm = (double)c->n * m;
+    {
+        ProfScope ps(K_XY_DF, true, st, 2.0 * 3 * nm * sizeof(double2) + 3.0 * c->n * sizeof(double),
+                     3 * nm * 5.0 * (mode == 0 ? 2.0 : 1.0) * (lg2(n1) + lg2(n2)));
+        k_xy2<double, dfc><<<(unsigned)(3LL * m * n3), th, smem2, st>>>(P, W, mode, lift_scale);
+    }
+    count_launch();
+    FAME_CUDA_TRY(c, cudaGetLastError());
+    return FAME_OK;
+}
+
+fame_status run_apply_c128(fame_ctx* c, const double2* y, double2* Ay, int m, bool df, cudaStream_t st) {
+    if (m <= 0) return FAME_OK;
+    if (!df || !c128_df_available(c, m)) return run_apply<double>(c, y, Ay, m, st);
+    fame_status s = grow(c, c->work, (size_t)m * 3 * (size_t)c->n * sizeof(dfc));
+    if (s != FAME_OK) return s;
+    const KParams<double> P = make_params<double>(c);
+    dfc* W = reinterpret_cast<dfc*>(c->work.p);
+    if ((s = z_pass_df(c, P, y, W, nullptr, nullptr, m, true, st)) != FAME_OK) return s;
+    if ((s = xy_df(c, P, W, m, 0, 0.0, st)) != FAME_OK) return s;
+    return z_pass_df(c, P, nullptr, nullptr, W, Ay, m, false, st);
+}
+
+fame_status run_lift_c128(fame_ctx* c, const double2* y, double2* x, int m, bool df, cudaStream_t st) {
+    if (m <= 0) return FAME_OK;
+    if (!df || !c128_df_available(c, m)) return run_lift<double>(c, y, x, m, st);
+    const KParams<double> P = make_params<double>(c);
+    dfc* W = reinterpret_cast<dfc*>(x);
+    fame_status s;
+    if ((s = z_pass_df(c, P, y, W, nullptr, nullptr, m, true, st)) != FAME_OK) return s;
+    return xy_df(c, P, W, m, 1, 1.0 / std::sqrt((double)c->n), st);
+}
+
 namespace {
 // H_j <- -i sqrt(lambda_j) H_j for the m fields [m][3n]
 __global__ void k_h_scale(double2* __restrict__ H, const double* __restrict__ w, int m, size_t N3) {
@@ -1036,7 +1147,7 @@ fame_status run_grad(fame_ctx* c, const double2* Y, const double* w, int nev, do
             any = any || w[j0 + j] != 0.0;
         }
         if (!any) continue;
-        if ((s = run_lift<double>(c, Y + (size_t)j0 * 2 * c->n, x, mc, st)) != FAME_OK) return s;
+        if ((s = run_lift_c128(c, Y + (size_t)j0 * 2 * c->n, x, mc, !fp64_native(), st)) != FAME_OK) return s;
         {
             ProfScope ps(K_GRAD, true, st, (double)N * (mc * sizeof(double2) + 2 * sizeof(double)), 4.0 * N * mc);
             k_grad_accum<<<1216, 256, 0, st>>>(x, gw, mc, dB, N);

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libfame.so")
 
-FAME_C64, FAME_C128 = 0, 1
+FAME_C64, FAME_C128, FAME_C128_DF = 0, 1, 2
 FAME_FP64, FAME_MIXED, FAME_DETERMINISTIC, FAME_WARM_START, FAME_INV_LANCZOS = 1, 2, 4, 8, 16
 STATUS = {0: "FAME_OK", 1: "FAME_E_ARG", 2: "FAME_E_LATTICE", 3: "FAME_E_RADIX", 4: "FAME_E_CUDA",
           5: "FAME_E_NOMEM", 6: "FAME_E_STATE", 7: "FAME_E_NOCONV", 8: "FAME_E_TIMEOUT"}
@@ -162,12 +162,14 @@ def _check_out(out, like):
         raise ValueError("out must be a CUDA tensor on the device of the input")
 
 
-def _dtype_code(t):
+def _dtype_code(t, double_float=False):
     import torch
     if t.dtype == torch.complex64:
+        if double_float:
+            raise TypeError("double_float applies to complex128 vectors")
         return FAME_C64
     if t.dtype == torch.complex128:
-        return FAME_C128
+        return FAME_C128_DF if double_float else FAME_C128
     raise TypeError("vectors must be complex64 or complex128")
 
 
@@ -247,8 +249,10 @@ class Context:
         _check(load().fame_set_eps_device(self._h, _ptr(B), _stream(stream)), self._h)
 
     # -- operator -----------------------------------------------------------
-    def apply(self, y, out=None, stream=None):
-        """A_r y for a complex CUDA tensor y of shape (m, 2n) (or (2n,))."""
+    def apply(self, y, out=None, stream=None, double_float=False):
+        """A_r y for a complex CUDA tensor y of shape (m, 2n) (or (2n,)).  With
+        double_float a complex128 y is transformed in double-float arithmetic
+        (FAME_C128_DF)."""
         import torch
         y = y.contiguous()
         m = y.numel() // (2 * self.N)
@@ -260,8 +264,8 @@ class Context:
             raise ValueError("out must have the shape and dtype of y")
         else:
             _check_out(out, y)
-        _check(load().fame_apply_Ar(self._h, _ptr(y), _ptr(out), m, _dtype_code(y), _stream(stream)),
-               self._h)
+        _check(load().fame_apply_Ar(self._h, _ptr(y), _ptr(out), m, _dtype_code(y, double_float),
+                                    _stream(stream)), self._h)
         return out
 
     def apply_static(self, y, out, stream=None):
@@ -344,13 +348,14 @@ class Context:
             os.replace(tmp, cache)
         return dict(entry, cached=False)
 
-    def lift(self, y, stream=None):
-        """x = B^{-1} Q_r Sigma_r y: (m, 2n) -> (m, 3n) complex on the Yee grid."""
+    def lift(self, y, stream=None, double_float=False):
+        """x = B^{-1} Q_r Sigma_r y: (m, 2n) -> (m, 3n) complex on the Yee grid (double_float:
+        as in apply)."""
         import torch
         y = y.contiguous()
         m = y.numel() // (2 * self.N)
         x = torch.empty((m, 3 * self.N), dtype=y.dtype, device=y.device)
-        _check(load().fame_lift(self._h, _ptr(y), _ptr(x), m, _dtype_code(y), _stream(stream)),
+        _check(load().fame_lift(self._h, _ptr(y), _ptr(x), m, _dtype_code(y, double_float), _stream(stream)),
                self._h)
         return x
 

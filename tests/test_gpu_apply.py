@@ -317,6 +317,35 @@ def test_fixed_length_variants_match_oracle(name, n):
     ctx.set_apply_plan(fame.FAME_C64)
 
 
+@pytest.mark.parametrize("name,n", [("fcc64", (16, 16, 16)),     # radix 2 lengths
+                                    ("tri192", (24, 20, 12)),   # triclinic twists, radix 3 and 5
+                                    ("mono80", (20, 24, 16)),
+                                    ("bcc96", (48, 48, 32))])    # a 48 x 48 plane per block
+def test_double_float_apply_and_lift_match_oracle(name, n):
+    """FAME_C128_DF: complex128 vectors transformed in double-float arithmetic on the FP32
+    units.  Its A_r y and lift agree with the oracle's FP64 results and with the FP64
+    kernels to 1e-12 of the largest entry (double-float rounds at about 2^-47), and the
+    profiler shows the double-float passes ran (no fallback to FP64)."""
+    lat, ctx, invB, rng = _setup(name, n, seed=8, margin=MARGIN["c128"])
+    m = 3
+    y = rng.standard_normal((m, 2 * lat.n)) + 1j * rng.standard_normal((m, 2 * lat.n))
+    yt = torch.as_tensor(y, dtype=torch.complex128, device="cuda")
+    fame.profile(True)
+    got = ctx.apply(yt, double_float=True).cpu().numpy()
+    x = ctx.lift(yt, double_float=True).cpu().numpy()
+    torch.cuda.synchronize()
+    fame.profile(False)
+    kinds = fame.profile_read()
+    assert {"zin_df_c128", "xy_df_c128", "zout_df_c128"} <= set(kinds), sorted(kinds)
+    nat = ctx.apply(yt).cpu().numpy()
+    for j in range(m):
+        ref = apply_Ar(lat, y[j].reshape((2,) + lat.shape), invB).ravel()
+        assert _rel(got[j], ref) < 1e-12, (j, _rel(got[j], ref))
+        assert _rel(got[j], nat[j]) < 1e-12
+        assert _rel(x[j], lift(lat, y[j].reshape((2,) + lat.shape), invB).ravel()) < 1e-12
+    ctx.close()
+
+
 def test_autotune_and_plan_cache(tmp_path):
     lat, ctx, invB, rng = _setup("fcc64", (32, 32, 48), seed=1)
     cache = str(tmp_path / "plans.json")
