@@ -264,7 +264,7 @@ FFT_PASSES = ("zin", "xy", "zout", "ypass", "xpass")
 
 
 KERNEL_SOURCES = ("apply3.cu", "blockops.cu", "transforms.cu", "eps.cu", "noalloc.cu", "tc_gram.cu", "precond.cu", "lanczos.cu", "tc.cuh", "fft2.cuh",
-                  "phases.cuh", "df64.cuh", "dfloat.cuh", "fame_internal.h", "blockops.h")
+                  "phases.cuh", "df64.cuh", "dfloat.cuh", "bounds.cuh", "fame_internal.h", "blockops.h")
 
 
 def kernel_source_hash():

@@ -375,6 +375,19 @@ FAME_API unsigned long long fame_launch_count(void);
 /* fame_version -- library version string. */
 FAME_API const char* fame_version(void);
 
+/*
+ * fame_bounds_violations -- for the bounds-checked debug build of the library
+ * (libfame_check.so, compiled with -DFAME_CHECK_BOUNDS; no counterpart in the
+ * paper).  In that build the kernels check the indices of their TMA boxes, of the
+ * FFT passes' global loads and stores and of the staged block copies before each
+ * access, skip an access that fails and record it.  Returns the number of failed
+ * checks since the previous call (and clears them); *code (may be NULL) receives
+ * the kind of the first (1 TMA coordinate, 2 tensor-core Gram output, 3 / 4 Z-pass
+ * load / store, 5 staged 16-byte copy, 6 refinement row, 7 two-level Z-pass store)
+ * and *index (may be NULL) its index.  Synchronous.  In the normal build: -1.
+ */
+FAME_API int fame_bounds_violations(int* code, long long* index);
+
 #ifdef __cplusplus
 }
 #endif

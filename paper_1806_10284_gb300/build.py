@@ -15,6 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libfame.so")
+# the bounds-checked debug build (-DFAME_CHECK_BOUNDS), built on request
+LIB_CHECK = os.path.join(OUT, "libfame_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fvisibility=hidden"]
@@ -31,20 +33,25 @@ def sources():
     return sorted(os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".cu", ".cpp")))
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
+def build(verbose: bool = False, force: bool = False, check_bounds: bool = False) -> str:
+    """Compile and link the library; with check_bounds the debug build with the kernels'
+    bounds checks (libfame_check.so, separate objects)."""
     os.makedirs(OUT, exist_ok=True)
+    lib = LIB_CHECK if check_bounds else LIB
     srcs = sources()
     deps = srcs + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(HERE, "..", "include", "fame.h"))
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= t for d in deps):
-            return LIB
+            return lib
     nvcc = _nvcc()
+    extra = ["-DFAME_CHECK_BOUNDS"] if check_bounds else []
+    suffix = ".check.o" if check_bounds else ".o"
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-x", "cu", "-c", src, "-o", obj]
+        obj = os.path.join(OUT, os.path.basename(src) + suffix)
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-x", "cu", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -54,14 +61,14 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, check_bounds="--check-bounds" in sys.argv))

@@ -1,3 +1,4 @@
+#include <algorithm>
 // C ABI entry points (declared in include/fame.h).
 #include <atomic>
 #include <cmath>
@@ -6,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "bounds.cuh"
 #include "fame_internal.h"
 
 namespace {
@@ -81,6 +83,32 @@ fame_status grow_pinned(fame_ctx* c, GrowBuf& b, size_t bytes) {
 extern "C" {
 
 const char* fame_version(void) { return "fame-gb300 0.1 (sm_103a)"; }
+
+int fame_bounds_violations(int* code, long long* index) {
+#ifdef FAME_CHECK_BOUNDS
+    const BoundsRec recs[] = {bounds_take_tc_gram(), bounds_take_apply3(), bounds_take_blockops(),
+                              bounds_take_transforms()};
+    long long total = 0;
+    bool first = true;
+    for (const BoundsRec& r : recs) {
+        total += r.count;
+        if (r.count && first) {
+            if (code) *code = r.code;
+            if (index) *index = r.index;
+            first = false;
+        }
+    }
+    if (first) {
+        if (code) *code = 0;
+        if (index) *index = 0;
+    }
+    return (int)std::min<long long>(total, 0x7fffffff);
+#else
+    if (code) *code = 0;
+    if (index) *index = 0;
+    return -1;
+#endif
+}
 
 unsigned long long fame_launch_count(void) { return g_launches.load(); }
 

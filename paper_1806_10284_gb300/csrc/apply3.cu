@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "bounds.cuh"
 #include "fame_internal.h"
 #include "fft2.cuh"
 #include "phases.cuh"
@@ -147,8 +148,9 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
 #pragma unroll
         for (int t1 = 0; t1 < R1; ++t1) {
             const size_t off = (size_t)(t + R2 * t1) * plane;
-            a1[t1] = valid ? yv[off] : mk((R)0, (R)0);
-            a2[t1] = valid ? yv[n + off] : mk((R)0, (R)0);
+            const bool ld_ok = valid && bounds_ok(base + off < n, kBndZLoad, (long long)(base + off));
+            a1[t1] = ld_ok ? yv[off] : mk((R)0, (R)0);
+            a2[t1] = ld_ok ? yv[n + off] : mk((R)0, (R)0);
         }
     };
     // with PF the first vector's loads are in flight while the tile tables are built
@@ -196,7 +198,8 @@ k_zin3(KParams<R> P, const typename cpx<R>::T* __restrict__ y, typename cpx<R>::
 #pragma unroll
                     for (int k2 = 0; k2 < R2; ++k2) {
                         const int c = k1 + R1 * k2;
-                        Wv[(size_t)l * n + (size_t)c * plane] = cmul(u[k2], T.tws[c][pp]);
+                        if (bounds_ok(base + (size_t)c * plane < n, kBndZStore, (long long)(base + (size_t)c * plane)))
+                            Wv[(size_t)l * n + (size_t)c * plane] = cmul(u[k2], T.tws[c][pp]);
                     }
                 }
             }
@@ -233,7 +236,10 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
         for (int l = 0; l < 3; ++l)
 #pragma unroll
             for (int t1 = 0; t1 < R1; ++t1)
-                g[l][t1] = valid ? Wv[(size_t)l * n + (size_t)(t + R2 * t1) * plane] : mk((R)0, (R)0);
+                g[l][t1] = (valid && bounds_ok(base + (size_t)(t + R2 * t1) * plane < n, kBndZLoad,
+                                               (long long)(base + (size_t)(t + R2 * t1) * plane)))
+                               ? Wv[(size_t)l * n + (size_t)(t + R2 * t1) * plane]
+                               : mk((R)0, (R)0);
     };
     // with PF the first vector's loads are in flight while the tile tables are built
     if (PF && t < R2 && blockIdx.z * vpc < v1) load(blockIdx.z * vpc);
@@ -269,8 +275,10 @@ k_zout3(KParams<R> P, const typename cpx<R>::T* __restrict__ W, typename cpx<R>:
                     const int r = k1 + R1 * k2;
                     C z1, z2;
                     contract<R>(T.PB[pp], T.L2[r][pp], (T.bits[r] >> pp) & 1u, u[0][k2], u[1][k2], u[2][k2], z1, z2);
-                    ov[(size_t)r * plane] = z1;
-                    ov[n + (size_t)r * plane] = z2;
+                    if (bounds_ok(base + (size_t)r * plane < n, kBndZStore, (long long)(base + (size_t)r * plane))) {
+                        ov[(size_t)r * plane] = z1;
+                        ov[n + (size_t)r * plane] = z2;
+                    }
                 }
             }
         }
@@ -539,6 +547,8 @@ fame_status launch_xy3(fame_ctx* c, const KParams<R>& P, typename cpx<R>::T* W, 
 }
 
 }  // namespace
+
+FAME_BOUNDS_READER(apply3)
 
 // Lengths with a fixed-length Z pass, and (n1, n2) pairs with a fixed-length XY pass.
 bool z3_supported(int L) { return L == 16 || L == 32 || L == 48 || L == 64 || L == 80 || L == 96; }

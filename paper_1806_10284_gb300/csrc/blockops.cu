@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "blockops.h"
+#include "bounds.cuh"
 #include "df64.cuh"
 
 // FP64 arithmetic on the FP64 units instead of double-float on the FP32 units (the
@@ -18,6 +19,8 @@ bool fp64_native() {
     const char* v = std::getenv("FAME_FP64_NATIVE");
     return v && v[0] == '1';
 }
+
+FAME_BOUNDS_READER(blockops)
 
 namespace {
 
@@ -723,7 +726,8 @@ __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(Bl
                 const int c = e / (kStRows / 2), rp = e - c * (kStRows / 2);
                 const int pos = p_chunk * kStCols + c;
                 const size_t row = p_tile * kStRows + 2 * (size_t)rp;
-                const bool ok = pos < k && row < ld;
+                // a 16-byte copy takes rows row and row + 1
+                const bool ok = pos < k && row < ld && bounds_ok(row + 2 <= ld, kBndRing, (long long)row);
                 cp_async16(dst + c * kStRows + 2 * rp, ok ? ps[pos] + row : ps[0], ok);
             }
         }
@@ -808,6 +812,7 @@ __global__ void __launch_bounds__(G * kStRows, (G == 1 ? 1 : 2)) k_combine_st(Bl
                     const int* b = blk + jj * (kRefBlk + 1);
                     float Sr = 0.f, Er = 0.f, Si = 0.f, Ei = 0.f;
                     for (int t = 0; t < b[0]; ++t) {
+                        if (!bounds_ok(b[1 + t] >= 0 && b[1 + t] < rf.mx, kBndXRows, b[1 + t])) continue;
                         const double2 x = xs[b[1 + t] * kStRows + rl];
                         const df64::Split xr = df64::split(x.x), xi = df64::split(x.y);
                         const float4 w = cfd[jj * kRefBlk + t];
@@ -868,7 +873,7 @@ __global__ void __launch_bounds__(G * kStRows) k_orth_st(const float2* __restric
                     const int i = (p_chunk - nqc) * kStCols + c;
                     if (i < m) src = X + (size_t)i * ld + row;
                 }
-                const bool ok = src != nullptr && row < ld;
+                const bool ok = src != nullptr && row < ld && bounds_ok(row + 2 <= ld, kBndRing, (long long)row);
                 cp_async16(dst + c * kStRows + 2 * rp, ok ? src : X, ok);
             }
         }

@@ -39,6 +39,7 @@
 #include <string>
 
 #include "blockops.h"
+#include "bounds.cuh"
 #include "tc.cuh"
 
 namespace {
@@ -66,6 +67,7 @@ struct TcGramArgs {
     int* err;
     unsigned long long timeout_ns;
     int skip_chunk;                    // test hook: this chunk is never loaded (-1: none)
+    int plant;                         // bounds-checked build, test hook: the first CTA's chunk 0 fails its TMA check
 };
 
 struct SmemLayout {
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const __grid_constant__
         if (lane == 0)
             for (int b = 0; b < a.nA + a.nB; ++b) tc::prefetch_tmap(&maps.m[b]);
         int issued = 0;
+        bool skipped0 = false;                                 // chunk 0 failed its bounds check
         for (int ch = 0; ch < nchunk; ++ch) {
             const int s = ch % NS;
             // lane 0 waits, the warp follows its verdict (no divergence around __syncwarp)
@@ -179,6 +182,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const __grid_constant__
                 break;
             }
             if (ch == a.skip_chunk) continue;                  // test hook: never delivered
+#ifdef FAME_CHECK_BOUNDS
+            {
+                // the box's x coordinate (floats) must start on a 16-byte boundary
+                const long long x = 2 * (long long)(row0 + (size_t)ch * KC);
+                const bool okx = lane == 0 ? bounds_ok((x & 3) == 0 && !(a.plant && ch == 0 && blockIdx.x == 0), kBndTmaX, x) : true;
+                if (__shfl_sync(0xffffffffu, okx ? 1 : 0, 0) == 0) {
+                    skipped0 = skipped0 || ch == 0;
+                    continue;                                  // not issued: the waits on it give up
+                }
+            }
+#endif
             if (lane == 0) tc::mbar_arrive_expect_tx(&full[s], a.raw_bytes);
             __syncwarp();
             if (lane < a.nA + a.nB) {
@@ -190,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const __grid_constant__
         // copies in flight must land before the CTA leaves
         if (lane == 0)
             for (int ch = std::max(0, issued - NS); ch < issued; ++ch) {
-                if (ch == a.skip_chunk) continue;
+                if (ch == a.skip_chunk || (ch == 0 && skipped0)) continue;
                 tc::mbar_wait(&full[ch % NS], (ch / NS) & 1, tc::global_ns() + tmo, never);
             }
     } else if (warp == 1) {
@@ -300,7 +314,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const __grid_constant__
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) {
                         const int bcol = bmap[j0 + jj];
-                        if (bcol >= 0) out[(size_t)bcol * a.MA + acol] = make_double2((double)re[jj], (double)im[jj]);
+                        if (bcol >= 0 && bounds_ok(bcol < a.NB && acol < a.MA, kBndTcOut, (long long)bcol * a.MA + acol))
+                            out[(size_t)bcol * a.MA + acol] = make_double2((double)re[jj], (double)im[jj]);
                     }
                 }
             }
@@ -438,7 +453,14 @@ int skip_chunk_hook() {
     return v ? std::atoi(v) : -1;
 }
 
+int plant_hook() {
+    const char* v = std::getenv("FAME_TEST_BOUNDS_PLANT");
+    return v && v[0] == '1' ? 1 : 0;
+}
+
 }  // namespace
+
+FAME_BOUNDS_READER(tc_gram)
 
 fame_status tc_reset_err(fame_ctx* c, cudaStream_t st) {
     fame_status s = grow(c, c->tcerr, 256);
@@ -527,6 +549,7 @@ fame_status gram_tc(fame_ctx* c, const BlockList<float2>& Ain, const BlockList<f
     a.err = reinterpret_cast<int*>(c->tcerr.p);
     a.timeout_ns = wait_timeout_ns();
     a.skip_chunk = skip_chunk_hook();
+    a.plant = plant_hook();
     if ((s = kernel_smem(c, (const void*)k_gram_tc, smem)) != FAME_OK) return s;
     {
         // algorithmic bytes: every distinct column read once; 8 flops per complex MAC

@@ -23,6 +23,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "bounds.cuh"
 #include "fame_internal.h"
 #include "dfloat.cuh"
 #include "fft2.cuh"
@@ -608,9 +609,9 @@ __global__ void __launch_bounds__(512) k_zin2(KParams<R> P, const typename cpx<R
             n3, NP, tw, Y, [&](int pc, int e) { return X[e * NP + pc]; },
             [&](int pc, int c, A val) {
                 const int l = pc >> lgTP, pp = pc & (TP - 1), p = p0 + pp;
-                if (p < n1)
-                    Wv[(size_t)l * n + ((size_t)c * n2 + q) * n1 + p] =
-                        cmul(val, as_arith<A>(P.tw3[((size_t)c * n2 + q) * n1 + p]));
+                const size_t o = (size_t)l * n + ((size_t)c * n2 + q) * n1 + p;
+                if (p < n1 && bounds_ok(o < 3 * n, kBndZ2Store, (long long)o))
+                    Wv[o] = cmul(val, as_arith<A>(P.tw3[((size_t)c * n2 + q) * n1 + p]));
             });
     }
 }
@@ -1010,6 +1011,8 @@ fame_status run_lift(fame_ctx* c, const typename cpx<R>::T* y, typename cpx<R>::
     if ((s = z_pass<R>(c, P, y, x, m, true, st)) != FAME_OK) return s;
     return xy_stage<R>(c, P, x, m, 1, (R)(1.0 / std::sqrt((double)c->n)), st);
 }
+
+FAME_BOUNDS_READER(transforms)
 
 // ---------------------------------------------------------------------------
 // Complex128 apply and lift in double-float arithmetic: the two-level passes with

@@ -15,6 +15,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libfame.so")
+# the bounds-checked debug build (build.build(check_bounds=True)); loaded instead of the
+# normal library when the environment sets FAME_CHECK_BOUNDS=1
+LIB_CHECK_PATH = os.path.join(_HERE, "_lib", "libfame_check.so")
 
 FAME_C64, FAME_C128, FAME_C128_DF = 0, 1, 2
 FAME_FP64, FAME_MIXED, FAME_DETERMINISTIC, FAME_WARM_START, FAME_INV_LANCZOS = 1, 2, 4, 8, 16
@@ -53,6 +56,7 @@ _SIGS = {
     "fame_destroy": (None, [C.c_void_p]),
     "fame_launch_count": (C.c_ulonglong, []),
     "fame_version": (C.c_char_p, []),
+    "fame_bounds_violations": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
 }
 
 
@@ -100,9 +104,12 @@ def profile_read():
                                        bytes=arr[i].bytes, flops=arr[i].flops) for i in range(k)}
 
 
-def load(path: str = LIB_PATH):
-    """Load the library (once).  Raises FameError if it is missing or incomplete."""
+def load(path: str = None):
+    """Load the library (once).  Raises FameError if it is missing or incomplete.  The
+    environment variable FAME_CHECK_BOUNDS=1 selects the bounds-checked build."""
     global _lib
+    if path is None:
+        path = LIB_CHECK_PATH if os.environ.get("FAME_CHECK_BOUNDS") == "1" else LIB_PATH
     with _lock:
         if _lib is not None:
             return _lib
@@ -147,6 +154,14 @@ def launch_count() -> int:
 
 def version() -> str:
     return load().fame_version().decode()
+
+
+def bounds_violations():
+    """(count, code, index) of the failed bounds checks since the previous call, cleared
+    (the bounds-checked build; count -1 in the normal build)."""
+    code, index = C.c_int(0), C.c_longlong(0)
+    n = load().fame_bounds_violations(C.byref(code), C.byref(index))
+    return int(n), int(code.value), int(index.value)
 
 
 def _ptr(t):

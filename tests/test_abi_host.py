@@ -38,6 +38,18 @@ def test_every_declared_symbol_exported(lib):
     assert sorted(fame.exported_symbols()) == header_symbols()
 
 
+def test_bounds_checked_build_links_and_exports_every_symbol(lib):
+    """The debug build with the kernels' bounds checks (-DFAME_CHECK_BOUNDS) compiles,
+    links and exports the same C ABI; the normal build reports -1 (no checks)."""
+    import ctypes
+    from paper_1806_10284_gb300 import build
+    path = build.build(check_bounds=True)
+    chk = ctypes.CDLL(path)
+    for s in header_symbols():
+        assert hasattr(chk, s), s
+    assert fame.bounds_violations() == (-1, 0, 0)
+
+
 def test_version_and_counter(lib):
     assert "sm_103a" in fame.version()
     assert fame.launch_count() >= 0
