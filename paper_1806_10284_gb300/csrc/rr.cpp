@@ -99,7 +99,9 @@ bool tridiag_qr(int k, std::vector<double>& d, std::vector<double>& e, std::vect
         const double mu = d[hi] - b2 / (delta + sgn * std::sqrt(delta * delta + b2));
         double x = d[lo] - mu, z = e[lo];
         for (int i = lo; i < hi; ++i) {
-            const double r = std::hypot(x, z);
+            // |(x, z)|: the plain root where the squares neither overflow nor underflow
+            double r = std::sqrt(x * x + z * z);
+            if (!(r > 1e-150 && r < 1e150)) r = std::hypot(x, z);
             const double c = (r == 0.0) ? 1.0 : x / r;
             const double s = (r == 0.0) ? 0.0 : z / r;
             if (i > lo) e[i - 1] = r;
@@ -112,8 +114,8 @@ bool tridiag_qr(int k, std::vector<double>& d, std::vector<double>& e, std::vect
                 e[i + 1] = c * e[i + 1];
             }
             x = e[i];
-            double* zi = &Z[(size_t)i * k];
-            double* zj = &Z[(size_t)(i + 1) * k];
+            double* __restrict__ zi = &Z[(size_t)i * k];
+            double* __restrict__ zj = &Z[(size_t)(i + 1) * k];
             for (int t = 0; t < k; ++t) {
                 const double u = zi[t], v = zj[t];
                 zi[t] = c * u + s * v;
