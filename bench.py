@@ -278,8 +278,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+def traffic_for(kernel, model_bytes_per_launch=None):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source.
+    Where the summary also gives the captured launch's algorithmic bytes, the traffic is
+    scaled to a launch of model_bytes_per_launch (the bench's launches of one kind process
+    blocks of different widths; traffic grows with the vectors processed)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
@@ -287,7 +290,13 @@ def traffic_for(kernel):
     if d.get("source_hash") != kernel_source_hash():
         return None
     k = d.get("kernels", {}).get(kernel)
-    return None if k is None else k.get("dram_bytes_per_launch")
+    if k is None:
+        return None
+    t = k.get("dram_bytes_per_launch")
+    cap = k.get("model_bytes_per_launch")
+    if t is not None and cap and model_bytes_per_launch:
+        t = t * model_bytes_per_launch / cap
+    return t
 
 
 def _bound(name, st):
@@ -321,7 +330,7 @@ def roofline(prof):
     bound, peak, unit, src = _bound(name, st)
     ach = st["bytes"] / secs / 1e9 if bound == "hbm" else st["flops"] / secs / 1e12
     return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-            "frac": ach / peak, "traffic": traffic_for(name), "peak_source": src,
+            "frac": ach / peak, "traffic": traffic_for(name, st["bytes"] / st["launches"]), "peak_source": src,
             "launches": st["launches"], "avg_launch_ms": st["total_ms"] / st["launches"],
             "bytes_per_launch": st["bytes"] / st["launches"],
             "flops_per_launch": st["flops"] / st["launches"],

@@ -54,7 +54,7 @@ def test_bound_of_each_kind(monkeypatch):
 
 
 def test_roofline_takes_dominant_kernel(monkeypatch):
-    monkeypatch.setattr(bench, "traffic_for", lambda name: None)
+    monkeypatch.setattr(bench, "traffic_for", lambda name, model_bytes=None: None)
     monkeypatch.setattr(bench, "measured_peaks", lambda: (6746.0, "measured"))
     r = bench.roofline(_prof())
     assert r["kernel"] == "gram_c64" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
@@ -75,12 +75,17 @@ def test_apply_roofline_counts_complex64_passes_only(monkeypatch):
 
 def test_traffic_only_for_matching_sources(monkeypatch, tmp_path):
     (tmp_path / "profiles").mkdir()
-    d = {"source_hash": "abc", "kernels": {"gram_c64": {"dram_bytes_per_launch": 1.25e8}}}
+    d = {"source_hash": "abc", "kernels": {"gram_c64": {"dram_bytes_per_launch": 1.25e8},
+                                          "xy_c64": {"dram_bytes_per_launch": 1.3e8,
+                                                     "model_bytes_per_launch": 2.0e8}}}
     (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(d))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
     assert bench.traffic_for("gram_c64") == 1.25e8
     assert bench.traffic_for("zin_c64") is None
+    # scaled to the bench's average launch by the ratio of the pass-model bytes
+    assert bench.traffic_for("xy_c64", 1.0e8) == pytest.approx(0.65e8)
+    assert bench.traffic_for("xy_c64") == 1.3e8
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "changed")
     assert bench.traffic_for("gram_c64") is None
 
