@@ -65,8 +65,8 @@ typedef enum {
  * vectors (the same memory layout as FAME_C128), transformed in double-float
  * arithmetic -- pairs of floats, about 48 significant bits -- on the FP32 units,
  * which on GB300 run FP64 work at 1/64 of their rate; results agree with FAME_C128
- * to about 1e-14 of the largest entry.  Grids whose x-y plane does not fit in
- * shared memory (the split y / x / y passes) take the FAME_C128 path instead.
+ * to about 1e-14 of the largest entry.  Grids whose z length has no two-level
+ * pass take the FAME_C128 path instead.
  * The eigensolver uses this form for its complex128 applies when the requested
  * residual is at least 1e-10 (environment FAME_FP64_NATIVE=1: never). */
 enum { FAME_C64 = 0, FAME_C128 = 1, FAME_C128_DF = 2 };

@@ -377,37 +377,36 @@ __global__ void __launch_bounds__(512) k_xy(KParams<R> P, typename cpx<R>::T* __
 // Split XY for planes that do not fit: y pass over x-tiles, x pass over rows.
 // y pass: grid (ceil(n1/TP), n3, 3m); dir 0 = inverse then D_a2, 1 = conj D_a2 then forward
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(256) k_ypass(KParams<R> P, typename cpx<R>::T* __restrict__ W,
-                                               int TP, int dir) {
-    using C = typename cpx<R>::T;
+template <typename R, typename A = typename cpx<R>::T>
+__global__ void __launch_bounds__(256) k_ypass(KParams<R> P, A* __restrict__ W, int TP, int dir) {
+    using Ar = decltype(A().x);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
     const size_t np = (size_t)n1 * n2;
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    C* buf = tw + n2;
-    C* buf2 = buf + n2 * TP;
+    A* tw = reinterpret_cast<A*>(smem_raw);
+    A* buf = tw + n2;
+    A* buf2 = buf + n2 * TP;
     const int p0 = blockIdx.x * TP, c = blockIdx.y;
-    C* g = W + ((size_t)blockIdx.z * n3 + c) * np;
-    load_table(tw, P.tw[1], n2);
+    A* g = W + ((size_t)blockIdx.z * n3 + c) * np;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) tw[i] = as_arith<A>(P.tw[1][i]);
     const int tile = n2 * TP;
     for (int e = threadIdx.x; e < tile; e += blockDim.x) {
         const int b = e / TP, pp = e - b * TP, p = p0 + pp;
-        C x = mk((R)0, (R)0);
+        A x = mk((Ar)0, (Ar)0);
         if (p < n1) {
             x = g[(size_t)b * n1 + p];
-            if (dir == 1) x = cmulc(P.tw2[(size_t)b * n1 + p], x);
+            if (dir == 1) x = cmulc(as_arith<A>(P.tw2[(size_t)b * n1 + p]), x);
         }
         buf[e] = x;
     }
     __syncthreads();
     const Pencils pen{TP, TP, 1, 0, TP, true};
-    const C* res = fft_axis(buf, buf2, pen, P.ax[1], tw, dir == 0);
+    const A* res = fft_axis(buf, buf2, pen, P.ax[1], tw, dir == 0);
     for (int e = threadIdx.x; e < tile; e += blockDim.x) {
         const int b = e / TP, pp = e - b * TP, p = p0 + pp;
         if (p < n1) {
-            C x = res[e];
-            if (dir == 0) x = cmul(x, P.tw2[(size_t)b * n1 + p]);
+            A x = res[e];
+            if (dir == 0) x = cmul(x, as_arith<A>(P.tw2[(size_t)b * n1 + p]));
             g[(size_t)b * n1 + p] = x;
         }
     }
@@ -415,38 +414,48 @@ __global__ void __launch_bounds__(256) k_ypass(KParams<R> P, typename cpx<R>::T*
 
 // x pass: RPB rows per block, grid ceil(3 m n3 n2 / RPB); mode 0 apply (inv, *B^{-1}/n, fwd),
 // mode 1 lift (inv, D_a1, *B^{-1} lift_scale)
-template <typename R>
-__global__ void __launch_bounds__(256) k_xpass(KParams<R> P, typename cpx<R>::T* __restrict__ W,
-                                               long long nrows, int RPB, int mode, R lift_scale) {
+// With A the double-float type, W holds double-float values on entry; mode 0 leaves
+// double-float values, modes 1 and 2 (the lift's last pass) write complex128.
+template <typename R, typename A = typename cpx<R>::T>
+__global__ void __launch_bounds__(256) k_xpass(KParams<R> P, A* __restrict__ W, long long nrows, int RPB,
+                                               int mode, R lift_scale) {
     using C = typename cpx<R>::T;
+    using Ar = decltype(A().x);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = P.n1, n2 = P.n2, n3 = P.n3;
-    C* tw = reinterpret_cast<C*>(smem_raw);
-    C* buf = tw + n1;
-    C* buf2 = buf + RPB * n1;
-    load_table(tw, P.tw[0], n1);
+    A* tw = reinterpret_cast<A*>(smem_raw);
+    A* buf = tw + n1;
+    A* buf2 = buf + RPB * n1;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) tw[i] = as_arith<A>(P.tw[0][i]);
     const long long r0 = (long long)blockIdx.x * RPB;
     const int nr = (int)min((long long)RPB, nrows - r0);
-    C* g = W + r0 * n1;
+    A* g = W + r0 * n1;
     for (int e = threadIdx.x; e < RPB * n1; e += blockDim.x)
-        buf[e] = (e < nr * n1) ? g[e] : mk((R)0, (R)0);
+        buf[e] = (e < nr * n1) ? g[e] : mk((Ar)0, (Ar)0);
     __syncthreads();
     const Pencils rows{RPB, 1, 0, n1, 1, false};
-    C* cur = fft_axis(buf, buf2, rows, P.ax[0], tw, true);
-    C* oth = (cur == buf) ? buf2 : buf;
+    A* cur = fft_axis(buf, buf2, rows, P.ax[0], tw, true);
+    A* oth = (cur == buf) ? buf2 : buf;
     const size_t nsp = (size_t)n1 * n2 * n3;
+    const Ar sc = as_arith_r<Ar>(P.scale), ls = as_arith_r<Ar>(lift_scale);
     for (int e = threadIdx.x; e < nr * n1; e += blockDim.x) {
         const long long row = r0 + e / n1;          // row = ((v*3 + l)*n3 + c)*n2 + b
         const int a = e % n1;
         const long long rb = row % ((long long)n3 * n2);
         const int l = (int)((row / ((long long)n3 * n2)) % 3);
-        const R ib = P.invB[(size_t)l * nsp + (size_t)rb * n1 + a];
-        if (mode == 0) cur[e] = (ib * P.scale) * cur[e];
-        else cur[e] = (mode == 2 ? lift_scale : ib * lift_scale) * cmul(cur[e], P.tw1[a]);
+        const Ar ib = as_arith_r<Ar>(P.invB[(size_t)l * nsp + (size_t)rb * n1 + a]);
+        if (mode == 0) cur[e] = (ib * sc) * cur[e];
+        else cur[e] = (mode == 2 ? ls : ib * ls) * cmul(cur[e], as_arith<A>(P.tw1[a]));
     }
     __syncthreads();
-    if (mode == 0) cur = fft_axis(cur, oth, rows, P.ax[0], tw, false);
-    for (int e = threadIdx.x; e < nr * n1; e += blockDim.x) g[e] = cur[e];
+    if (mode == 0) {
+        cur = fft_axis(cur, oth, rows, P.ax[0], tw, false);
+        for (int e = threadIdx.x; e < nr * n1; e += blockDim.x) g[e] = cur[e];
+    } else {
+        // the complex128 result goes over the double-float input in place (same size)
+        C* gc = reinterpret_cast<C*>(g);
+        for (int e = threadIdx.x; e < nr * n1; e += blockDim.x) gc[e] = as_store<C>(cur[e]);
+    }
 }
 
 // weights of up to kGradChunk lifted bands
@@ -1020,9 +1029,8 @@ FAME_BOUNDS_READER(transforms)
 // passes holds double-float values (the same 16 bytes per complex entry).
 // ---------------------------------------------------------------------------
 bool c128_df_available(const fame_ctx* c, int m) {
-    const int n1 = c->plan.n[0], n2 = c->plan.n[1];
-    return z2_config<double>(c, m).ok && fft2::supported(n1) && fft2::supported(n2) &&
-           xy2_smem<double>(n1, n2) <= kSmemCap;
+    // the two-level Z passes; the XY stage as one plane kernel or as y / x / y passes
+    return z2_config<double>(c, m).ok;
 }
 
 static fame_status z_pass_df(fame_ctx* c, const KParams<double>& P, const double2* y, dfc* W,
@@ -1051,6 +1059,40 @@ static fame_status xy_df(fame_ctx* c, const KParams<double>& P, dfc* W, int m, i
                          cudaStream_t st) {
     const int n1 = c->plan.n[0], n2 = c->plan.n[1], n3 = c->plan.n[2];
     const size_t smem2 = xy2_smem<double>(n1, n2);
+    if (!(fft2::supported(n1) && fft2::supported(n2) && smem2 <= kSmemCap)) {
+        // the plane does not fit: y pass, x pass (B^{-1} or the lift), y pass
+        int TPy = 16;
+        while (TPy > 1 && (size_t)(n2 + 2 * TPy * n2) * sizeof(dfc) > kSmemCap) TPy /= 2;
+        const size_t ysm = (size_t)(n2 + 2 * TPy * n2) * sizeof(dfc);
+        fame_status s = set_smem<double>(c, (const void*)k_ypass<double, dfc>, ysm);
+        if (s != FAME_OK) return s;
+        int RPB = 16;
+        while (RPB > 1 && (size_t)(n1 + 2 * RPB * n1) * sizeof(dfc) > kSmemCap) RPB /= 2;
+        const size_t xsm = (size_t)(n1 + 2 * RPB * n1) * sizeof(dfc);
+        if ((s = set_smem<double>(c, (const void*)k_xpass<double, dfc>, xsm)) != FAME_OK) return s;
+        const long long nrows = 3LL * m * n3 * n2;
+        const double nm = (double)c->n * m;
+        dim3 yg((n1 + TPy - 1) / TPy, n3, 3 * m);
+        const double ybytes = 2.0 * 3 * nm * sizeof(double2);
+        {
+            ProfScope ps(K_XY_DF, true, st, ybytes, 3 * nm * 5.0 * lg2(n2));
+            k_ypass<double, dfc><<<yg, 256, ysm, st>>>(P, W, TPy, 0);
+        }
+        {
+            ProfScope ps(K_XY_DF, true, st, ybytes + 3.0 * c->n * sizeof(double),
+                         3 * nm * 5.0 * lg2(n1) * (mode == 0 ? 2.0 : 1.0));
+            k_xpass<double, dfc><<<(unsigned)((nrows + RPB - 1) / RPB), 256, xsm, st>>>(P, W, nrows, RPB, mode,
+                                                                                      lift_scale);
+        }
+        count_launch(2);
+        if (mode == 0) {
+            ProfScope ps(K_XY_DF, true, st, ybytes, 3 * nm * 5.0 * lg2(n2));
+            k_ypass<double, dfc><<<yg, 256, ysm, st>>>(P, W, TPy, 1);
+            count_launch();
+        }
+        FAME_CUDA_TRY(c, cudaGetLastError());
+        return FAME_OK;
+    }
     fame_status s = set_smem<double>(c, (const void*)k_xy2<double, dfc>, smem2);
     if (s != FAME_OK) return s;
     const fft2::Split sx = fft2::split_of(n1), sy = fft2::split_of(n2);

@@ -320,7 +320,8 @@ def test_fixed_length_variants_match_oracle(name, n):
 @pytest.mark.parametrize("name,n", [("fcc64", (16, 16, 16)),     # radix 2 lengths
                                     ("tri192", (24, 20, 12)),   # triclinic twists, radix 3 and 5
                                     ("mono80", (20, 24, 16)),
-                                    ("bcc96", (48, 48, 32))])    # a 48 x 48 plane per block
+                                    ("bcc96", (48, 48, 32)),    # a 48 x 48 plane per block
+                                    ("hex96", (96, 96, 8))])     # 96 x 96 planes: y / x / y passes
 def test_double_float_apply_and_lift_match_oracle(name, n):
     """FAME_C128_DF: complex128 vectors transformed in double-float arithmetic on the FP32
     units.  Its A_r y and lift agree with the oracle's FP64 results and with the FP64
